@@ -1,0 +1,228 @@
+/*
+ * lms.h - C ABI of liblms: GB300 Laplacian mesh smoothing with
+ * locality-aware vertex orderings.
+ *
+ * Method: Aupy, Park & Raghavan, "Locality-Aware Laplacian Mesh Smoothing".
+ *   - smoothing step: Eq. 1 (a vertex moves to the mean of its N mesh
+ *     neighbours), applied to interior vertices only (Algorithm 1);
+ *   - quality: Section 3.2 (edge-length ratio of a triangle, mean over a
+ *     vertex's triangles, mean over all |V| vertices);
+ *   - stopping rule: Section 5.1 (stop once the global quality improves by
+ *     less than a criterion, 5e-6 in the paper) plus an iteration cap
+ *     (Section 3.2);
+ *   - orderings: original, random, breadth-first, and the Reuse Distance
+ *     Reducing ordering of Algorithm 2 (Section 4.2), compared in Section 5.2.
+ *
+ * Conventions for every entry point:
+ *   - ids are int32, vertices 0..n-1 in the caller's (original) labelling;
+ *   - coordinates are interleaved doubles: xy[2v] = x, xy[2v+1] = y;
+ *   - inputs are host pointers and are copied; the caller keeps ownership;
+ *     outputs go to caller-allocated host buffers;
+ *   - every int-returning call returns LMS_OK (0) or a negative LMS_ERR_*;
+ *     lms_error_string() gives a message;
+ *   - device work is issued on the CUDA stream given at creation (NULL = the
+ *     legacy default stream); calls that return host data synchronise that
+ *     stream first;
+ *   - a handle is not thread-safe; distinct handles are independent.
+ *
+ * Entry points marked [host] do no device work and need no GPU.
+ */
+#ifndef LMS_H
+#define LMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LMS_OK 0
+#define LMS_ERR_ARG (-1)          /* NULL pointer, bad enum, n <= 0, out-of-range index, non-finite coordinate */
+#define LMS_ERR_CSR (-2)          /* row_ptr not monotone / not starting at 0, id out of range, self-loop,
+                                     duplicate entry, or adjacency not symmetric */
+#define LMS_ERR_ISOLATED (-3)     /* interior vertex with no neighbour: Eq. 1 would divide by zero */
+#define LMS_ERR_NO_TRIANGLES (-4) /* quality, RDR or a stopping rule requested without triangles */
+#define LMS_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define LMS_ERR_OOM (-6)          /* host or device allocation failed */
+#define LMS_ERR_TIMEOUT (-7)      /* a bounded device-side wait gave up */
+#define LMS_ERR_STATE (-8)        /* call not valid in the handle's current state */
+
+/* precision of the stored coordinates and of the sweep arithmetic */
+#define LMS_FP64 0 /* double2 coordinates, FP64 sums and division (results equal the FP64 sequential sums) */
+#define LMS_FP32 1 /* float2 coordinates relative to the bounding-box centre, scaled by the larger box
+                      side; compensated (Kahan) FP32 neighbour sums; quality reduced in FP64 */
+
+/* vertex orderings (Section 5.2.1 compares ORI, BFS and RDR; Fig. 1 adds a random one) */
+#define LMS_ORI 0    /* original order: identity permutation */
+#define LMS_RANDOM 1 /* Fisher-Yates shuffle driven by splitmix64(seed) */
+#define LMS_BFS 2    /* breadth-first visit order from vertex 0, neighbours by ascending id,
+                        restarting at the smallest unvisited id */
+#define LMS_RDR 3    /* Algorithm 2: walks from the worst-quality interior vertex, appending
+                        unordered neighbours by increasing (quality, id) */
+
+/* sweep modes */
+#define LMS_JACOBI 0     /* all interior vertices read the previous sweep's positions (ping-pong) */
+#define LMS_COLORED_GS 1 /* in place, colour by colour of a first-fit colouring of the interior vertices
+                            in storage order; equals Algorithm 1's sequential in-place sweep taken in
+                            (colour, storage position) order */
+
+typedef struct lms_mesh_s* lms_handle;
+typedef struct lms_batch_s* lms_batch;
+
+/* one mesh of a batch; all pointers are host pointers, copied by lms_batch_create */
+typedef struct {
+    int32_t n;                   /* vertices */
+    const int32_t* row_ptr;      /* [n+1] CSR offsets, row_ptr[0] = 0 */
+    const int32_t* col_idx;      /* [row_ptr[n]] symmetric adjacency, no self-loops or duplicates */
+    const double* xy;            /* [2n] coordinates */
+    const uint8_t* is_boundary;  /* [n] nonzero = fixed vertex */
+    int32_t ntri;                /* triangles (may be 0 when tri is NULL) */
+    const int32_t* tri;          /* [3 ntri] corner ids, or NULL */
+} lms_mesh_desc;
+
+/* Text for a status code (static storage). [host] */
+const char* lms_error_string(int status);
+
+/*
+ * Route the library's device allocations through caller-supplied functions
+ * (for example a framework's caching allocator).  alloc(bytes, stream, ctx)
+ * returns a device pointer or NULL; release(ptr, ctx) frees it.  Passing NULL
+ * for both restores cudaMalloc/cudaFree.  Affects handles created afterwards;
+ * a handle frees with the functions it allocated with.  [host]
+ */
+int lms_set_device_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
+                             void (*release)(void* ptr, void* ctx), void* ctx);
+
+/*
+ * Check a mesh without creating anything.  Returns LMS_OK, LMS_ERR_ARG,
+ * LMS_ERR_CSR or LMS_ERR_ISOLATED; tri may be NULL when ntri == 0. [host]
+ */
+int lms_validate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                 int32_t ntri, const int32_t* tri);
+
+/*
+ * Vertex ordering on the host (Section 4.2, Algorithm 2; Section 5.2.1).
+ * q_v: [n] per-vertex quality (Section 3.2), required for LMS_RDR and ignored
+ * otherwise.  new_to_old: [n] output, new_to_old[k] = original id stored at
+ * position k; always a permutation (Theorem 1; vertices no RDR walk reaches
+ * are appended in ascending id).  [host]
+ */
+int lms_order_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const double* q_v, int ordering, uint64_t seed, int32_t* new_to_old);
+
+/*
+ * First-fit colouring of the interior vertices visited in storage order
+ * new_to_old.  colour: [n] output indexed by original id (-1 for boundary
+ * vertices); *ncolours receives the colour count.  [host]
+ */
+int lms_color_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const int32_t* new_to_old, int32_t* colour, int32_t* ncolours);
+
+/*
+ * Create a smoothing handle: validates the mesh (as lms_validate), copies it
+ * to the device and stores the coordinates in `precision`.  The initial
+ * ordering is LMS_ORI.  tri may be NULL (ntri = 0); quality, LMS_RDR and the
+ * stopping rule then return LMS_ERR_NO_TRIANGLES.  cuda_stream: a
+ * cudaStream_t or NULL.
+ */
+int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* xy,
+               const uint8_t* is_boundary, int32_t ntri, const int32_t* tri, int precision,
+               void* cuda_stream, lms_handle* out);
+
+/*
+ * Store the mesh under an ordering (Section 4.2 / 5.2.1): computes the
+ * permutation on the host (RDR keys are the per-vertex qualities of the
+ * current coordinates, computed on the device in FP64) and relabels the
+ * device CSR, coordinates and triangles.  Rows keep their entry order, so
+ * Jacobi results do not depend on the ordering.  seed is used by LMS_RANDOM.
+ */
+int lms_reorder(lms_handle h, int ordering, uint64_t seed);
+
+/*
+ * Smooth: up to max_iters sweeps of `mode` (Eq. 1 on every interior vertex).
+ * tol < 0: exactly max_iters sweeps (asynchronous; *iters_done = max_iters).
+ * tol >= 0: Algorithm 1 with the Section 5.1 rule - Q_0 is computed first and
+ * the loop stops after sweep k when Q_k - Q_{k-1} < tol (signed), or at
+ * max_iters; synchronous.  The last sweep also records the largest vertex
+ * displacement (see lms_last_stats).  iters_done may be NULL.
+ */
+int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done);
+
+/* Global mesh quality Q (Section 3.2, FP64 reduction) of the current coordinates. */
+int lms_quality(lms_handle h, double* Q);
+
+/* Current coordinates in the original labelling: [2n] doubles (FP32 storage is mapped back exactly
+   as x = c + s * x_hat in FP64; before any sweep the values passed in are returned unchanged). */
+int lms_get_coords(lms_handle h, double* xy);
+
+/* Replace the coordinates ([2n], original labelling); the ordering is kept. */
+int lms_set_coords(lms_handle h, const double* xy);
+
+/* Current ordering: [n] new_to_old. */
+int lms_get_permutation(lms_handle h, int32_t* new_to_old);
+
+/* Colouring used by LMS_COLORED_GS for the current ordering ([n], original labelling, -1 = boundary).
+   Computed on first use. */
+int lms_get_colors(lms_handle h, int32_t* colour, int32_t* ncolours);
+
+/* Device CSR in the current ordering, downloaded: row_ptr [n+1], col_idx [nnz] (for checks). */
+int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx);
+
+/* Statistics of the last lms_smooth: largest vertex displacement of its final sweep (original units),
+   device time in ms, Q before and after (NaN when no stopping rule ran).  Any pointer may be NULL. */
+int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, double* q_last);
+
+/* Free a handle and its device memory (NULL is ignored). */
+void lms_destroy(lms_handle h);
+
+/*
+ * Batched FP32 smoothing of many independent meshes in one persistent
+ * work-queue kernel per sweep.  Each mesh is stored under `ordering`
+ * (computed as lms_reorder does), normalised by its own bounding box, and cut
+ * into vertex tiles that never cross a mesh boundary; CTAs pull tiles from a
+ * device counter.  Launch parameters come from the autotuner unless set with
+ * lms_batch_set_config.
+ */
+int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint64_t seed, void* cuda_stream,
+                     lms_batch* out);
+
+/* `iters` Jacobi sweeps of every mesh, recorded once into a CUDA graph and replayed (asynchronous). */
+int lms_batch_smooth(lms_batch b, int32_t iters);
+
+/* Coordinates of mesh `mesh` in its original labelling ([2 n_mesh] doubles). */
+int lms_batch_get_coords(lms_batch b, int32_t mesh, double* xy);
+
+/* All meshes' coordinates, concatenated in mesh order, original labelling ([2 sum n] doubles). */
+int lms_batch_get_all_coords(lms_batch b, double* xy);
+
+/* Replace all meshes' coordinates (concatenated as above); the orderings are kept. */
+int lms_batch_set_all_coords(lms_batch b, const double* xy);
+
+/* Totals: vertices, interior vertices, CSR entries, tiles (any pointer may be NULL). [no device work] */
+int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles);
+
+/*
+ * Launch configuration of the batched sweep: block = threads per CTA,
+ * lanes = lanes per vertex (1, 2 or 4), tile = vertices per work item,
+ * ctas_per_sm = resident CTAs the persistent grid assumes.
+ * lms_batch_autotune times the candidates on the batch (without changing its
+ * coordinates), keeps the fastest, and returns it; results are cached in the
+ * file named by the LMS_AUTOTUNE_CACHE environment variable when it is set.
+ */
+int lms_batch_get_config(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm);
+int lms_batch_set_config(lms_batch b, int32_t block, int32_t lanes, int32_t tile, int32_t ctas_per_sm);
+int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm);
+
+/* Kernel launches recorded in the last lms_batch_smooth / lms_smooth graph. [no device work] */
+int lms_batch_last_launches(lms_batch b, int64_t* launches);
+int lms_last_launches(lms_handle h, int64_t* launches);
+
+void lms_batch_destroy(lms_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LMS_H */

@@ -1,0 +1,431 @@
+/*
+ * lms_oracle.c - plain, slow, single-threaded FP64 reference for Laplacian
+ * mesh smoothing (LMS) and its vertex orderings.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  It shares no code with the
+ * CUDA library and must never be called from the product path.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no -ffast-math): every
+ * floating-point operation below is one IEEE-754 round-to-nearest operation
+ * in the order written.
+ *
+ * What each function follows (Aupy, Park & Raghavan, "Locality-Aware
+ * Laplacian Mesh Smoothing"):
+ *   or_triangle_quality / or_vertex_quality / or_mesh_quality - Section 3.2:
+ *       edge-length ratio (shortest over longest edge) per triangle, the mean
+ *       over the triangles attached to a vertex, the mean over all |V|
+ *       vertices (Algorithm 1 divides the summed quality by |V|).
+ *   or_jacobi_sweep - Eq. 1 applied to every interior vertex from the old
+ *       positions (simultaneous update; boundary vertices keep their place).
+ *   or_inplace_sweep - Algorithm 1's inner loop: interior vertices visited in
+ *       a given sequence, each moved by Eq. 1 using the current positions.
+ *   or_smooth - Algorithm 1's outer loop with the stopping rule of Section
+ *       5.1 (stop once the global quality improves by less than a criterion)
+ *       and an iteration cap (Section 3.2 notes that one exists).
+ *   or_order_random / or_order_bfs / or_order_rdr - the orderings compared in
+ *       Section 5.2: a seeded random permutation, breadth-first search, and
+ *       the Reuse Distance Reducing ordering of Algorithm 2.
+ *   or_relabel - storing the mesh under an ordering (the node array of the
+ *       Section 5.2.3 footnote, relabelled).
+ *   or_color_greedy - first-fit colouring of the interior vertices in
+ *       storage order; the sequence "colour by colour, storage order inside a
+ *       colour" is the in-place sweep that a coloured Gauss-Seidel reproduces.
+ *
+ * Readings where the paper is silent (the same list is kept with the design
+ * notes):
+ *   - neighbour sums run left to right over the stored row, x and y
+ *     separately, starting from 0.0; the mean is one IEEE division by the
+ *     neighbour count;
+ *   - a triangle whose longest edge has length 0 has quality 0; a vertex with
+ *     no triangle has quality 0 and still counts in |V|;
+ *   - the quality mean of a vertex sums its triangles in ascending triangle id;
+ *     the mesh mean sums vertices in ascending id;
+ *   - RDR sort key is (quality, vertex id) ascending; neighbour lists include
+ *     boundary vertices; l[0] is the first (worst-quality) member of l;
+ *     vertices never reached are appended in ascending id at the end;
+ *   - BFS starts at vertex 0, visits neighbours in ascending id and restarts
+ *     at the smallest unvisited id when the queue empties;
+ *   - RANDOM is a Fisher-Yates shuffle driven by splitmix64 (Steele, Lea &
+ *     Flood, OOPSLA 2014) seeded with the given seed;
+ *   - the stopping rule stops after sweep k when Q_k >= goal or
+ *     Q_k - Q_{k-1} < tol (a signed difference).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG -1
+#define OR_ERR_OOM -2
+
+/* ---------------------------------------------------------------- quality */
+
+/* Section 3.2: shortest edge length divided by longest edge length. */
+static double triangle_quality(const double* xy, int32_t a, int32_t b, int32_t c) {
+    const int32_t v[3] = {a, b, c};
+    double len[3];
+    for (int e = 0; e < 3; ++e) {
+        int32_t p = v[e], q = v[(e + 1) % 3];
+        double dx = xy[2 * q] - xy[2 * p];
+        double dy = xy[2 * q + 1] - xy[2 * p + 1];
+        len[e] = sqrt(dx * dx + dy * dy);
+    }
+    double lo = len[0], hi = len[0];
+    for (int e = 1; e < 3; ++e) {
+        if (len[e] < lo) lo = len[e];
+        if (len[e] > hi) hi = len[e];
+    }
+    if (hi == 0.0) return 0.0;
+    return lo / hi;
+}
+
+int or_triangle_quality(int32_t ntri, const int32_t* tri, const double* xy, double* q_t) {
+    if (ntri < 0 || (ntri > 0 && (!tri || !xy || !q_t))) return OR_ERR_ARG;
+    for (int32_t t = 0; t < ntri; ++t)
+        q_t[t] = triangle_quality(xy, tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]);
+    return OR_OK;
+}
+
+/* Section 3.2: a vertex's quality is the mean quality of its triangles. */
+int or_vertex_quality(int32_t n, int32_t ntri, const int32_t* tri, const double* xy, double* q_v) {
+    if (n <= 0 || ntri < 0 || !xy || !q_v || (ntri > 0 && !tri)) return OR_ERR_ARG;
+    double* sum = (double*)calloc((size_t)n, sizeof(double));
+    int32_t* cnt = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+    if (!sum || !cnt) { free(sum); free(cnt); return OR_ERR_OOM; }
+    for (int32_t t = 0; t < ntri; ++t) {               /* ascending triangle id */
+        double q = triangle_quality(xy, tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]);
+        for (int k = 0; k < 3; ++k) {
+            int32_t v = tri[3 * t + k];
+            sum[v] = sum[v] + q;
+            cnt[v] += 1;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) q_v[v] = cnt[v] > 0 ? sum[v] / (double)cnt[v] : 0.0;
+    free(sum); free(cnt);
+    return OR_OK;
+}
+
+/* Algorithm 1: the global quality is the summed vertex quality over |V|. */
+int or_mesh_quality(int32_t n, int32_t ntri, const int32_t* tri, const double* xy, double* Q) {
+    if (!Q) return OR_ERR_ARG;
+    double* q_v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!q_v) return OR_ERR_OOM;
+    int rc = or_vertex_quality(n, ntri, tri, xy, q_v);
+    if (rc == OR_OK) {
+        double s = 0.0;
+        for (int32_t v = 0; v < n; ++v) s = s + q_v[v];
+        *Q = s / (double)n;
+    }
+    free(q_v);
+    return rc;
+}
+
+/* ---------------------------------------------------------------- sweeps */
+
+/* Eq. 1 for vertex v, reading positions from src: mean of the neighbours. */
+static void laplacian_point(const int32_t* row_ptr, const int32_t* col_idx, const double* src,
+                            int32_t v, double* px, double* py) {
+    double sx = 0.0, sy = 0.0;
+    int32_t N = row_ptr[v + 1] - row_ptr[v];
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        int32_t u = col_idx[e];
+        sx = sx + src[2 * u];
+        sy = sy + src[2 * u + 1];
+    }
+    *px = sx / (double)N;
+    *py = sy / (double)N;
+}
+
+/* One simultaneous (Jacobi) sweep: dst = Eq. 1 of src on interior vertices, src elsewhere. */
+int or_jacobi_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const double* src, double* dst) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !src || !dst || src == dst) return OR_ERR_ARG;
+    for (int32_t v = 0; v < n; ++v) {
+        if (is_boundary[v]) {
+            dst[2 * v] = src[2 * v];
+            dst[2 * v + 1] = src[2 * v + 1];
+        } else {
+            laplacian_point(row_ptr, col_idx, src, v, &dst[2 * v], &dst[2 * v + 1]);
+        }
+    }
+    return OR_OK;
+}
+
+/* Algorithm 1's inner loop: visit seq[0..nseq) in order, smoothing each interior vertex in place. */
+int or_inplace_sweep(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                     int32_t nseq, const int32_t* seq, double* xy) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !xy || nseq < 0 || (nseq > 0 && !seq)) return OR_ERR_ARG;
+    for (int32_t i = 0; i < nseq; ++i) {
+        int32_t v = seq[i];
+        if (v < 0 || v >= n) return OR_ERR_ARG;
+        if (is_boundary[v]) continue;
+        double px, py;
+        laplacian_point(row_ptr, col_idx, xy, v, &px, &py);
+        xy[2 * v] = px;
+        xy[2 * v + 1] = py;
+    }
+    return OR_OK;
+}
+
+/*
+ * Algorithm 1 with the stopping rule.  mode 0: Jacobi sweeps; mode 1: in-place
+ * sweeps over seq.  tol < 0: exactly max_iters sweeps, no quality.  Otherwise
+ * Q_0 is computed first and after sweep k the loop stops when Q_k >= goal or
+ * Q_k - Q_{k-1} < tol.  q_hist (optional, max_iters + 1 entries) receives
+ * Q_0..Q_k.  *iters receives the number of sweeps done.
+ */
+int or_smooth(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+              int32_t ntri, const int32_t* tri, double* xy, int32_t max_iters, int32_t mode,
+              int32_t nseq, const int32_t* seq, double tol, double goal, int32_t* iters, double* q_hist) {
+    if (n <= 0 || !xy || !iters || max_iters < 0 || (mode != 0 && mode != 1)) return OR_ERR_ARG;
+    if (tol >= 0.0 && (ntri <= 0 || !tri)) return OR_ERR_ARG;
+    double* tmp = NULL;
+    if (mode == 0) {
+        tmp = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+        if (!tmp) return OR_ERR_OOM;
+    }
+    double q_prev = 0.0;
+    int rc = OR_OK;
+    if (tol >= 0.0) {
+        rc = or_mesh_quality(n, ntri, tri, xy, &q_prev);
+        if (rc != OR_OK) goto done;
+        if (q_hist) q_hist[0] = q_prev;
+    }
+    *iters = 0;
+    for (int32_t k = 1; k <= max_iters; ++k) {
+        if (mode == 0) {
+            rc = or_jacobi_sweep(n, row_ptr, col_idx, is_boundary, xy, tmp);
+            if (rc != OR_OK) goto done;
+            memcpy(xy, tmp, sizeof(double) * 2 * (size_t)n);
+        } else {
+            rc = or_inplace_sweep(n, row_ptr, col_idx, is_boundary, nseq, seq, xy);
+            if (rc != OR_OK) goto done;
+        }
+        *iters = k;
+        if (tol >= 0.0) {
+            double q;
+            rc = or_mesh_quality(n, ntri, tri, xy, &q);
+            if (rc != OR_OK) goto done;
+            if (q_hist) q_hist[k] = q;
+            if (q >= goal || q - q_prev < tol) break;
+            q_prev = q;
+        }
+    }
+done:
+    free(tmp);
+    return rc;
+}
+
+/* ------------------------------------------------------------- orderings */
+
+static uint64_t splitmix64(uint64_t* state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* RANDOM: Fisher-Yates over 0..n-1, new_to_old[k] = original id stored at position k. */
+int or_order_random(int32_t n, uint64_t seed, int32_t* new_to_old) {
+    if (n <= 0 || !new_to_old) return OR_ERR_ARG;
+    for (int32_t i = 0; i < n; ++i) new_to_old[i] = i;
+    uint64_t st = seed;
+    for (int32_t i = n - 1; i >= 1; --i) {
+        int32_t j = (int32_t)(splitmix64(&st) % (uint64_t)(i + 1));
+        int32_t t = new_to_old[i]; new_to_old[i] = new_to_old[j]; new_to_old[j] = t;
+    }
+    return OR_OK;
+}
+
+static int cmp_int32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* BFS: visit order of a breadth-first search from vertex 0, neighbours by ascending id. */
+int or_order_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* new_to_old) {
+    if (n <= 0 || !row_ptr || !col_idx || !new_to_old) return OR_ERR_ARG;
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    int32_t* nb = (int32_t*)malloc(sizeof(int32_t) * 64);
+    if (!seen || !nb) { free(seen); free(nb); return OR_ERR_OOM; }
+    int32_t nb_cap = 64, head = 0, tail = 0;
+    for (int32_t root = 0; root < n; ++root) {
+        if (seen[root]) continue;
+        seen[root] = 1;
+        new_to_old[tail++] = root;
+        while (head < tail) {
+            int32_t v = new_to_old[head++];
+            int32_t len = row_ptr[v + 1] - row_ptr[v];
+            if (len > nb_cap) {
+                int32_t* g = (int32_t*)realloc(nb, sizeof(int32_t) * (size_t)len);
+                if (!g) { free(seen); free(nb); return OR_ERR_OOM; }
+                nb = g; nb_cap = len;
+            }
+            memcpy(nb, col_idx + row_ptr[v], sizeof(int32_t) * (size_t)len);
+            qsort(nb, (size_t)len, sizeof(int32_t), cmp_int32);
+            for (int32_t e = 0; e < len; ++e) {
+                int32_t u = nb[e];
+                if (!seen[u]) { seen[u] = 1; new_to_old[tail++] = u; }
+            }
+        }
+    }
+    free(seen); free(nb);
+    return OR_OK;
+}
+
+/* RDR sort key: (quality, id) ascending */
+static const double* g_key_q;
+static int key_less(int32_t a, int32_t b) {
+    if (g_key_q[a] < g_key_q[b]) return 1;
+    if (g_key_q[a] > g_key_q[b]) return 0;
+    return a < b;
+}
+static int cmp_key(const void* pa, const void* pb) {
+    int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+    if (a == b) return 0;
+    return key_less(a, b) ? -1 : 1;
+}
+
+/* l <- unprocessed neighbours of v sorted by increasing quality; returns |l| */
+static int32_t unprocessed_neighbours(const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* processed,
+                                      int32_t v, int32_t* l) {
+    int32_t m = 0;
+    for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+        if (!processed[col_idx[e]]) l[m++] = col_idx[e];
+    qsort(l, (size_t)m, sizeof(int32_t), cmp_key);
+    return m;
+}
+
+/*
+ * Algorithm 2 (Reuse Distance Reducing ordering).  q_v: per-vertex quality.
+ * For every interior vertex i in increasing quality that is not processed yet:
+ * order i if needed, mark it processed, then walk: l = its unprocessed
+ * neighbours by increasing quality; order the members of l not yet ordered;
+ * mark l[0] processed and continue from l[0] until l is empty.
+ */
+int or_order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                 const double* q_v, int32_t* new_to_old) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !q_v || !new_to_old) return OR_ERR_ARG;
+    int32_t max_deg = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > max_deg) max_deg = row_ptr[v + 1] - row_ptr[v];
+    uint8_t* processed = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* sorted = (uint8_t*)calloc((size_t)n, 1);
+    int32_t* interior = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* l = (int32_t*)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    if (!processed || !sorted || !interior || !l) {
+        free(processed); free(sorted); free(interior); free(l);
+        return OR_ERR_OOM;
+    }
+    g_key_q = q_v;
+    int32_t ni = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (!is_boundary[v]) interior[ni++] = v;
+    qsort(interior, (size_t)ni, sizeof(int32_t), cmp_key);
+
+    int32_t next_num = 0;
+    for (int32_t ii = 0; ii < ni; ++ii) {
+        int32_t i = interior[ii];
+        if (processed[i]) continue;
+        if (!sorted[i]) {
+            new_to_old[next_num++] = i;
+            sorted[i] = 1;
+        }
+        processed[i] = 1;
+        int32_t m = unprocessed_neighbours(row_ptr, col_idx, processed, i, l);
+        while (m > 0) {
+            for (int32_t j = 0; j < m; ++j) {
+                if (!sorted[l[j]]) {
+                    new_to_old[next_num++] = l[j];
+                    sorted[l[j]] = 1;
+                }
+            }
+            int32_t w = l[0];
+            processed[w] = 1;
+            m = unprocessed_neighbours(row_ptr, col_idx, processed, w, l);
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)            /* vertices no walk reached */
+        if (!sorted[v]) { new_to_old[next_num++] = v; sorted[v] = 1; }
+    free(processed); free(sorted); free(interior); free(l);
+    return next_num == n ? OR_OK : OR_ERR_ARG;
+}
+
+/* ----------------------------------------------------------- relabelling */
+
+/*
+ * Store the mesh under an ordering: new row k is the old row new_to_old[k]
+ * with every id mapped to its new position; entry order inside a row is kept.
+ */
+int or_relabel(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* new_to_old,
+               int32_t* out_row_ptr, int32_t* out_col_idx) {
+    if (n <= 0 || !row_ptr || !col_idx || !new_to_old || !out_row_ptr || !out_col_idx) return OR_ERR_ARG;
+    int32_t* old_to_new = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!old_to_new) return OR_ERR_OOM;
+    for (int32_t k = 0; k < n; ++k) old_to_new[new_to_old[k]] = k;
+    out_row_ptr[0] = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t v = new_to_old[k];
+        int32_t len = row_ptr[v + 1] - row_ptr[v];
+        for (int32_t e = 0; e < len; ++e) out_col_idx[out_row_ptr[k] + e] = old_to_new[col_idx[row_ptr[v] + e]];
+        out_row_ptr[k + 1] = out_row_ptr[k] + len;
+    }
+    free(old_to_new);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------- colouring */
+
+/*
+ * First-fit colouring of the interior vertices, visited in storage order
+ * new_to_old[0..n): each gets the smallest colour not used by an interior
+ * neighbour coloured before it.  colour[] is indexed by original id; boundary
+ * vertices get -1.  Returns the number of colours in *ncolours.
+ */
+int or_color_greedy(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !new_to_old || !colour || !ncolours) return OR_ERR_ARG;
+    int32_t max_deg = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > max_deg) max_deg = row_ptr[v + 1] - row_ptr[v];
+    uint8_t* used = (uint8_t*)calloc((size_t)max_deg + 2, 1);
+    if (!used) return OR_ERR_OOM;
+    for (int32_t v = 0; v < n; ++v) colour[v] = -1;
+    int32_t nc = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t v = new_to_old[k];
+        if (is_boundary[v]) continue;
+        memset(used, 0, (size_t)max_deg + 2);
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t c = colour[col_idx[e]];
+            if (c >= 0 && c <= max_deg) used[c] = 1;
+        }
+        int32_t c = 0;
+        while (used[c]) ++c;
+        colour[v] = c;
+        if (c + 1 > nc) nc = c + 1;
+    }
+    free(used);
+    *ncolours = nc;
+    return OR_OK;
+}
+
+/*
+ * The in-place sequence a coloured Gauss-Seidel sweep reproduces: interior
+ * vertices sorted by (colour, storage position).  seq receives original ids;
+ * returns the count in *nseq.
+ */
+int or_color_sequence(int32_t n, const uint8_t* is_boundary, const int32_t* new_to_old, const int32_t* colour,
+                      int32_t ncolours, int32_t* seq, int32_t* nseq) {
+    if (n <= 0 || !is_boundary || !new_to_old || !colour || !seq || !nseq || ncolours < 0) return OR_ERR_ARG;
+    int32_t m = 0;
+    for (int32_t c = 0; c < ncolours; ++c)
+        for (int32_t k = 0; k < n; ++k) {
+            int32_t v = new_to_old[k];
+            if (!is_boundary[v] && colour[v] == c) seq[m++] = v;
+        }
+    *nseq = m;
+    return OR_OK;
+}
