@@ -1,0 +1,507 @@
+#!/usr/bin/env python
+"""Benchmark of the Laplacian mesh smoothing hot path on GB300.
+
+Headline (one JSON line on rank 0): batched FP32 Jacobi smoothing of 512
+independent synthetic meshes (jittered grids with 10% interior-edge flips and
+5% centroid splits, sides log-uniform in [32, 448], ~21M vertices), each in
+the RDR ordering (Algorithm 2); one step = 50 sweeps replayed from one CUDA
+graph of persistent work-queue launches.  value = interior-vertex updates per
+second over the timed steps (inputs resident in HBM); e2e = the same metric
+through the public API with page-locked host buffers (coordinates in, 50
+sweeps, coordinates out).  Beside it: the FP64 plain path and every ordering on
+the 1024 x 1024 workload (~1.15M vertices, 100 sweeps), the roofline of the
+dominant kernel, the oracle timed on host cores, clocks under load.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--full]
+
+Under torchrun (N > 1) every rank smooths its own 512-mesh batch (weak
+scaling, no collective on the data path); timings are max-reduced over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertex updates/s and % HBM roofline: FP32 batched vs FP64 plain, per ordering"
+UNIT = "vertex updates/s"
+SWEEPS_PER_STEP = 50
+PER_ORDERING_SWEEPS = 100
+L2_BYTES = 129 * 2 ** 20
+FP64_OPS_PEAK_NOTE = "2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s counting an FMA as 2)"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--meshes", type=int, default=512)
+    ap.add_argument("--full", action="store_true", help="also time the 4096 x 4096 workload (FP64 vs FP32)")
+    ap.add_argument("--skip-extras", action="store_true", help="headline only (no per-ordering table)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Dist:
+    """Barrier and max-over-ranks for timings; a no-op at world size 1."""
+
+    def __init__(self, backend=None):
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+            self.backend = backend
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x):
+        if self.pg is None:
+            return float(x)
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x):
+        if self.pg is None:
+            return float(x)
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+def rank_mesh_seeds(count, rank):
+    """Seeds of the meshes rank `rank` smooths: rank 0 has the 512-mesh workload itself; other ranks
+    get as many different meshes of the same size distribution (weak scaling)."""
+    import meshgen
+    base = meshgen.BASE_SEED + 3 + 1000
+    return [base + rank * count + m for m in range(count)]
+
+
+def batch_for_rank(count, rank):
+    import meshgen
+    sides = meshgen.batch_sides(count)
+    seeds = rank_mesh_seeds(count, rank)
+    return [meshgen.generate(s, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=sd) for s, sd in zip(sides, seeds)]
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def algorithmic_bytes_fp32(n, n_int, nnz, k=1):
+    """Per sweep, every array element moved once: row_ptr 4(n+k), col_idx 4 nnz, positions read 8n,
+    positions written 8 n_int, boundary bits n/8."""
+    return 4 * (n + k) + 4 * nnz + 8 * n + 8 * n_int + n / 8.0
+
+
+def algorithmic_bytes_fp64(n, n_int, nnz, k=1):
+    return 4 * (n + k) + 4 * nnz + 16 * n + 16 * n_int + n / 8.0
+
+
+def fp64_ops(n_int, nnz_int):
+    """FP64 instructions of one FP64 sweep: two adds per neighbour entry, three per division (x, y)."""
+    return 2 * nnz_int + 6 * n_int
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        busy = [s for s, p in zip(sm, power) if p > 200] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def cpu_rate_oracle(meshes, sweeps, budget_s):
+    """Oracle Jacobi (single thread) over a prefix of `meshes` within ~budget_s; returns (rate, sample)."""
+    import oracle
+    updates, spent, used, verts = 0, 0.0, 0, 0
+    for m in meshes:
+        n_int = int((m["is_boundary"] == 0).sum())
+        t = time.perf_counter()
+        oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps)
+        spent += time.perf_counter() - t
+        updates += n_int * sweeps
+        used += 1
+        verts += m["n"]
+        if spent >= budget_s:
+            break
+    return updates / spent, dict(meshes=used, vertices=verts, sweeps=sweeps, seconds=spent)
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def time_graph(fn, stream, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def per_ordering_table(hbm_peak):
+    """1024 x 1024 workload: every ordering x {FP64, FP32} x {Jacobi, coloured GS}, 100 sweeps."""
+    import torch
+    import meshgen
+    import paper_1606_00803_gb300 as lms
+    m = meshgen.workload(1)
+    n, nnz = m["n"], m["nnz"]
+    n_int = int((m["is_boundary"] == 0).sum())
+    deg = m["row_ptr"][1:] - m["row_ptr"][:-1]
+    nnz_int = int(deg[m["is_boundary"] == 0].sum())
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for oname, o in (("ori", lms.ORI), ("random", lms.RANDOM), ("bfs", lms.BFS), ("rdr", lms.RDR)):
+        for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
+            g = lms.Mesh.from_dict(m, p)
+            t0 = time.perf_counter()
+            g.reorder(o, seed=meshgen.BASE_SEED + 7)
+            reorder_ms = (time.perf_counter() - t0) * 1e3
+            for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
+                g.smooth(PER_ORDERING_SWEEPS, mode=mode)  # warm-up + graph capture
+                torch.cuda.synchronize()
+                ms = min(time_graph(lambda: g.smooth(PER_ORDERING_SWEEPS, mode=mode), stream, 1) for _ in range(3))
+                sweep_ms = ms / PER_ORDERING_SWEEPS
+                ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
+                gbs = ab / (sweep_ms * 1e-3) / 1e9
+                row = dict(updates_per_s=n_int / (sweep_ms * 1e-3), sweep_ms=round(sweep_ms, 5),
+                           algorithmic_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 3))
+                if mode == lms.COLORED_GS:
+                    row["colours"] = g.colors()[1]
+                if p == lms.FP64:
+                    ops = fp64_ops(n_int, nnz_int) / (sweep_ms * 1e-3)
+                    row["fp64_ops_per_s"] = ops
+                rows["%s/%s/%s" % (oname, pname, mname)] = row
+            rows["%s/%s/reorder_ms" % (oname, pname)] = round(reorder_ms, 1)
+            g.close()
+    return dict(workload="1024x1024 jittered grid + 10%% flips + 5%% splits (%d vertices, %d interior, %d CSR "
+                         "entries), %d sweeps; working set fits in L2 at FP32, so GB/s may exceed HBM" %
+                         (n, n_int, nnz, PER_ORDERING_SWEEPS), rows=rows)
+
+
+def large_table(hbm_peak):
+    """4096 x 4096 workload (~18.4M vertices): RANDOM vs RDR, FP64 vs FP32, Jacobi and coloured GS."""
+    import torch
+    import meshgen
+    import paper_1606_00803_gb300 as lms
+    m = meshgen.workload(4)
+    n, nnz = m["n"], m["nnz"]
+    n_int = int((m["is_boundary"] == 0).sum())
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for oname, o in (("random", lms.RANDOM), ("rdr", lms.RDR)):
+        for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
+            g = lms.Mesh.from_dict(m, p)
+            g.reorder(o, seed=meshgen.BASE_SEED + 7)
+            for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
+                g.smooth(20, mode=mode)
+                torch.cuda.synchronize()
+                ms = min(time_graph(lambda: g.smooth(20, mode=mode), stream, 1) for _ in range(3)) / 20
+                ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
+                gbs = ab / (ms * 1e-3) / 1e9
+                rows["%s/%s/%s" % (oname, pname, mname)] = dict(
+                    updates_per_s=n_int / (ms * 1e-3), sweep_ms=round(ms, 4), algorithmic_gbs=round(gbs, 1),
+                    hbm_frac=round(gbs / hbm_peak, 3))
+            g.close()
+    return dict(workload="4096x4096 jittered grid + flips/splits (%d vertices), 20-sweep graphs" % n, rows=rows)
+
+
+def log(msg):
+    sys.stderr.write("[bench] %s\n" % msg)
+    sys.stderr.flush()
+
+
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+    import paper_1606_00803_gb300 as lms
+
+    torch.cuda.set_device(dist.local if dist.world > 1 else 0)
+    hbm_peak, peak_kind = measured_peaks()
+    meshes = batch_for_rank(args.meshes, dist.rank)
+    t0 = time.perf_counter()
+    b = lms.Batch(meshes, ordering=lms.RDR)
+    create_s = time.perf_counter() - t0
+    log("batch of %d meshes created in %.2f s" % (len(meshes), create_s))
+    t0 = time.perf_counter()
+    cfg = b.autotune()
+    tune_s = time.perf_counter() - t0
+    log("autotune %.2f s: %s" % (tune_s, cfg))
+    info = b.info()
+    n, n_int, nnz, k = info["n_total"], info["n_interior"], info["nnz_total"], len(meshes)
+    ab = algorithmic_bytes_fp32(n, n_int, nnz, k)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        b.smooth(SWEEPS_PER_STEP)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_uuid())
+    sampler.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    ms_local = e0.elapsed_time(e1)
+    ms_total = dist.max(ms_local)
+    launches_per_step = b.last_launches()
+    ms_step = ms_total / args.steps
+    units_all = dist.sum(n_int * SWEEPS_PER_STEP * args.steps)
+    value = units_all / (ms_total * 1e-3)
+    sweep_ms = ms_local / (args.steps * launches_per_step)
+    achieved = ab / (sweep_ms * 1e-3) / 1e9
+
+    # end to end through the public API: page-locked host coordinates in, 50 sweeps, coordinates out
+    xy_in = torch.from_numpy(np.concatenate([m["xy"] for m in meshes])).pin_memory()
+    xy_out = torch.empty_like(xy_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        b.set_all_coords(xy_in)
+        b.smooth(SWEEPS_PER_STEP)
+        b.all_coords(xy_out.numpy())
+
+    e2e_step()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_local = time.perf_counter() - t0
+    e2e_s = dist.max(e2e_local)
+    e2e_value = dist.sum(n_int * SWEEPS_PER_STEP * e2e_steps) / e2e_s
+    log("headline: %.4g updates/s, %.3f ms/step, sweep %.4f ms, %.1f GB/s algorithmic (%.3f of peak); e2e %.4g"
+        % (value, ms_step, sweep_ms, achieved, achieved / hbm_peak, e2e_value))
+    h2d = int(xy_in.numel() * 8)
+    d2h = int(xy_out.numel() * 8)
+
+    extras = {}
+    if dist.rank == 0 and not args.skip_extras:
+        extras["per_ordering"] = per_ordering_table(hbm_peak)
+        rdr = extras["per_ordering"]["rows"]["rdr/fp64/jacobi"]
+        extras["fp64_plain"] = dict(
+            workload="1024x1024, RDR, Jacobi, 100 sweeps", updates_per_s=rdr["updates_per_s"],
+            roofline=dict(bound="alu", achieved=rdr["fp64_ops_per_s"] / 1e9, peak=2 * 152 * 2.07,
+                          unit="G FP64 instr/s", frac=round(rdr["fp64_ops_per_s"] / 1e9 / (2 * 152 * 2.07), 3),
+                          peak_note=FP64_OPS_PEAK_NOTE),
+            hbm_frac=rdr["hbm_frac"])
+        if args.full:
+            extras["large"] = large_table(hbm_peak)
+    cpu = None
+    if dist.rank == 0 and dist.world == 1:
+        rate, sample = cpu_rate_oracle(meshes, SWEEPS_PER_STEP, 10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d of the %d meshes (%d vertices), %d Jacobi sweeps each, FP64, one thread, %.1f s"
+                         % (sample["meshes"], k, sample["vertices"], sample["sweeps"], sample["seconds"])}
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": "batched FP32 Jacobi: %d meshes (jittered grid, 10%% flips, 5%% centroid splits, side "
+                            "log-uniform 32..448), RDR ordering, %d sweeps per step replayed from one CUDA graph"
+                            % (k, SWEEPS_PER_STEP),
+                "meshes": k, "vertices": n, "interior_vertices": n_int, "csr_entries": nnz,
+                "sweeps_per_step": SWEEPS_PER_STEP, "ordering": "rdr", "precision": "fp32 (Kahan sums)",
+                "l2": "inputs larger than L2: %.2f GB moved per sweep vs 129 MB L2" % (ab / 1e9),
+                "launch": cfg, "parallelism": "each rank smooths its own batch" if dist.world > 1 else "1 GPU",
+                "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_batch_sweep<%d>" % cfg["lanes"],
+                         "algorithmic_bytes_per_launch": ab, "launch_ms": sweep_ms,
+                         "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 7900.0},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "ms_per_step": e2e_s * 1e3 / e2e_steps},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+        }
+        line.update(extras)
+        traffic = load_traffic()
+        if traffic is not None:
+            line["roofline"]["traffic"] = traffic
+        print(json.dumps(line))
+    b.close()
+
+
+def load_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        return t.get("k_batch_sweep_dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args, dist):
+    """The oracle as it stands, on the host cores, over a bounded sample of the same workload."""
+    if dist.rank != 0:
+        return
+    meshes = batch_for_rank(args.meshes, 0)
+    import oracle
+    # size the per-step sample so that (warmup + steps) steps take about a minute
+    per_step_s = max(0.05, 60.0 / (args.steps + max(3, args.warmup)))
+    probe_rate, _ = cpu_rate_oracle(meshes[:1], SWEEPS_PER_STEP, 0.0)
+    budget = per_step_s * probe_rate
+    sample, updates = [], 0
+    for m in meshes:
+        u = int((m["is_boundary"] == 0).sum()) * SWEEPS_PER_STEP
+        if sample and updates + u > budget:
+            break
+        sample.append(m)
+        updates += u
+
+    def step():
+        for m in sample:
+            oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], SWEEPS_PER_STEP)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = updates * args.steps / dt
+    desc = ("first %d of the %d meshes (%d vertices), %d Jacobi sweeps each, FP64 oracle, one thread"
+            % (len(sample), len(meshes), sum(m["n"] for m in sample), SWEEPS_PER_STEP))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched Jacobi: %d meshes (jittered grid, 10%% flips, 5%% centroid splits, side "
+                               "log-uniform 32..448), RDR ordering, %d sweeps per step; each step a bounded sample"
+                               % (len(meshes), SWEEPS_PER_STEP), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        rank, world, _ = dist_env()
+        if rank != 0:
+            return
+        class _D:  # the reference arm runs on rank 0 alone, without a process group
+            pass
+        d = _D()
+        d.rank, d.world = 0, world
+        run_reference(args, d)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    dist = Dist()
+    try:
+        run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

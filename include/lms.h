@@ -157,7 +157,9 @@ int lms_quality(lms_handle h, double* Q);
    as x = c + s * x_hat in FP64; before any sweep the values passed in are returned unchanged). */
 int lms_get_coords(lms_handle h, double* xy);
 
-/* Replace the coordinates ([2n], original labelling); the ordering is kept. */
+/* Replace the coordinates ([2n], original labelling); the ordering is kept.  The copy is issued on the
+   handle's stream: a page-locked xy must stay valid until that stream has reached it (any call that
+   returns host data synchronises it). */
 int lms_set_coords(lms_handle h, const double* xy);
 
 /* Current ordering: [n] new_to_old. */
@@ -167,8 +169,11 @@ int lms_get_permutation(lms_handle h, int32_t* new_to_old);
    Computed on first use. */
 int lms_get_colors(lms_handle h, int32_t* colour, int32_t* ncolours);
 
-/* Device CSR in the current ordering, downloaded: row_ptr [n+1], col_idx [nnz] (for checks). */
-int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx);
+/* Device CSR of the current storage layout, downloaded: row_ptr [n+1], col_idx [nnz]; the layout's
+   new_to_old [n] goes to storage_new_to_old when it is not NULL.  After lms_reorder the layout is the
+   ordering's; after an LMS_COLORED_GS sweep it is the coloured layout (interior vertices grouped by
+   colour, each group in the ordering's order, then the boundary vertices). */
+int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx, int32_t* storage_new_to_old);
 
 /* Statistics of the last lms_smooth: largest vertex displacement of its final sweep (original units),
    device time in ms, Q before and after (NaN when no stopping rule ran).  Any pointer may be NULL. */
@@ -176,6 +181,16 @@ int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, 
 
 /* Free a handle and its device memory (NULL is ignored). */
 void lms_destroy(lms_handle h);
+
+/* Text of the last CUDA error seen by this thread (empty if none). [host] */
+const char* lms_last_error_detail(void);
+
+/*
+ * Diagnostic of the FP64 sweep's division: q[i] = s[i] / d[i] (d[i] >= 1) computed on the device by the
+ * same table-driven routine the sweep uses (reciprocal RN(1/d), product, one fused correction).  Every
+ * q[i] must equal the IEEE quotient.  Host arrays of `count` entries.
+ */
+int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q);
 
 /*
  * Batched FP32 smoothing of many independent meshes in one persistent
@@ -215,7 +230,10 @@ int lms_batch_get_config(lms_batch b, int32_t* block, int32_t* lanes, int32_t* t
 int lms_batch_set_config(lms_batch b, int32_t block, int32_t lanes, int32_t tile, int32_t ctas_per_sm);
 int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm);
 
-/* Kernel launches recorded in the last lms_batch_smooth / lms_smooth graph. [no device work] */
+/* Ordering of mesh `mesh` of a batch ([n_mesh] new_to_old, local ids).  LMS_RANDOM uses seed + mesh. */
+int lms_batch_get_permutation(lms_batch b, int32_t mesh, int32_t* new_to_old);
+
+/* Kernel launches issued by the last lms_batch_smooth / lms_smooth. [no device work] */
 int lms_batch_last_launches(lms_batch b, int64_t* launches);
 int lms_last_launches(lms_handle h, int64_t* launches);
 

@@ -1,0 +1,419 @@
+"""GB300 Laplacian mesh smoothing with locality-aware vertex orderings.
+
+Thin Python binding of the C ABI in ``include/lms.h`` (liblms.so, built
+in-tree by ``_build.build()``).  This module only marshals arguments: every
+step of the method runs in the library (host orderings in C++, sweeps,
+quality reductions and relabelling in sm_103a kernels).  There is no Python or
+CPU fallback; a missing library raises.
+
+PyTorch, when present with a GPU, supplies the CUDA stream (the current
+stream at call time) and the device memory (the library allocates through
+torch's caching allocator).
+
+Method: Aupy, Park & Raghavan, "Locality-Aware Laplacian Mesh Smoothing"
+(Eq. 1, Algorithm 1, Section 3.2 quality, Section 5.1 stopping rule,
+Algorithm 2 RDR ordering).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FP64, FP32 = 0, 1
+ORI, RANDOM, BFS, RDR = 0, 1, 2, 3
+JACOBI, COLORED_GS = 0, 1
+ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR}
+MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS}
+PRECISIONS = {"fp64": FP64, "fp32": FP32}
+
+LMS_OK = 0
+ERRORS = {-1: "LMS_ERR_ARG", -2: "LMS_ERR_CSR", -3: "LMS_ERR_ISOLATED", -4: "LMS_ERR_NO_TRIANGLES",
+          -5: "LMS_ERR_CUDA", -6: "LMS_ERR_OOM", -7: "LMS_ERR_TIMEOUT", -8: "LMS_ERR_STATE"}
+
+
+class LmsError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = "%s failed: %s (%s)" % (where, ERRORS.get(status, status), _lib().lms_error_string(status).decode())
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_D = ctypes.c_double
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PD = ctypes.POINTER(ctypes.c_double)
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n", _I32), ("row_ptr", _P), ("col_idx", _P), ("xy", _P), ("is_boundary", _P), ("ntri", _I32),
+                ("tri", _P)]
+
+
+_SIGS = {
+    "lms_error_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lms_last_error_detail": ([], ctypes.c_char_p),
+    "lms_set_device_allocator": ([_P, _P, _P], ctypes.c_int),
+    "lms_validate": ([_I32, _P, _P, _P, _I32, _P], ctypes.c_int),
+    "lms_order_host": ([_I32, _P, _P, _P, _P, ctypes.c_int, _U64, _P], ctypes.c_int),
+    "lms_color_host": ([_I32, _P, _P, _P, _P, _P, _PI32], ctypes.c_int),
+    "lms_create": ([_I32, _P, _P, _P, _P, _I32, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "lms_reorder": ([_P, ctypes.c_int, _U64], ctypes.c_int),
+    "lms_smooth": ([_P, _I32, ctypes.c_int, _D, _PI32], ctypes.c_int),
+    "lms_quality": ([_P, _PD], ctypes.c_int),
+    "lms_get_coords": ([_P, _P], ctypes.c_int),
+    "lms_set_coords": ([_P, _P], ctypes.c_int),
+    "lms_get_permutation": ([_P, _P], ctypes.c_int),
+    "lms_get_colors": ([_P, _P, _PI32], ctypes.c_int),
+    "lms_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
+    "lms_last_stats": ([_P, _PD, _PD, _PD, _PD], ctypes.c_int),
+    "lms_last_launches": ([_P, _PI64], ctypes.c_int),
+    "lms_destroy": ([_P], None),
+    "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
+    "lms_batch_create": ([_I32, ctypes.POINTER(MeshDesc), ctypes.c_int, _U64, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "lms_batch_smooth": ([_P, _I32], ctypes.c_int),
+    "lms_batch_get_coords": ([_P, _I32, _P], ctypes.c_int),
+    "lms_batch_get_all_coords": ([_P, _P], ctypes.c_int),
+    "lms_batch_set_all_coords": ([_P, _P], ctypes.c_int),
+    "lms_batch_info": ([_P, _PI64, _PI64, _PI64, _PI32], ctypes.c_int),
+    "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32], ctypes.c_int),
+    "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_get_permutation": ([_P, _I32, _P], ctypes.c_int),
+    "lms_batch_last_launches": ([_P, _PI64], ctypes.c_int),
+    "lms_batch_destroy": ([_P], None),
+}
+
+_handle = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def _lib():
+    """Load liblms.so, building it first when it is missing or stale."""
+    global _handle
+    if _handle is None:
+        # launch configurations picked by lms_batch_autotune persist next to the library
+        os.environ.setdefault("LMS_AUTOTUNE_CACHE", os.path.join(_build.OUT_DIR, "autotune_cache.txt"))
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _handle = lib
+        _install_torch_allocator(lib)
+    return _handle
+
+
+def _check(status, where):
+    if status != LMS_OK:
+        detail = _lib().lms_last_error_detail().decode(errors="replace")
+        raise LmsError(status, where, detail)
+
+
+# ---------------------------------------------------------------- torch plumbing
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_callbacks = []
+
+
+def _torch_cuda():
+    try:
+        import torch
+        return torch if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+def _install_torch_allocator(lib):
+    torch = _torch_cuda()
+    if torch is None or os.environ.get("LMS_NO_TORCH_ALLOCATOR"):
+        return
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    a, f = _ALLOC_T(alloc), _FREE_T(free)
+    _callbacks.append((a, f))
+    _check(lib.lms_set_device_allocator(ctypes.cast(a, _P), ctypes.cast(f, _P), None), "lms_set_device_allocator")
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream (0 = legacy default stream when torch has no GPU)."""
+    torch = _torch_cuda()
+    return int(torch.cuda.current_stream().cuda_stream) if torch is not None else 0
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor (e.g. page-locked host buffer)
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host_f64(xy, n):
+    if hasattr(xy, "data_ptr"):
+        if xy.is_cuda or str(xy.dtype) != "torch.float64" or not xy.is_contiguous() or xy.numel() != 2 * n:
+            raise ValueError("coordinates must be a contiguous host float64 tensor of 2n values")
+        return xy
+    a = _arr(xy, np.float64)
+    if a.size != 2 * n:
+        raise ValueError("expected %d coordinates, got %d" % (2 * n, a.size))
+    return a
+
+
+def validate(row_ptr, col_idx, is_boundary, tri=None):
+    """lms_validate: LMS_OK or a negative status (no exception)."""
+    rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
+    t = _arr(tri, np.int32) if tri is not None else None
+    return _lib().lms_validate(len(rp) - 1, _ptr(rp), _ptr(ci), _ptr(b), 0 if t is None else t.size // 3, _ptr(t))
+
+
+def order_host(row_ptr, col_idx, is_boundary, ordering, seed=0, q_v=None):
+    """lms_order_host: new_to_old of ORI / RANDOM / BFS / RDR (RDR needs q_v)."""
+    rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
+    q = _arr(q_v, np.float64) if q_v is not None else None
+    n = len(rp) - 1
+    out = np.empty(n, np.int32)
+    _check(_lib().lms_order_host(n, _ptr(rp), _ptr(ci), _ptr(b), _ptr(q), int(ordering), seed & (2**64 - 1),
+                                 _ptr(out)), "lms_order_host")
+    return out
+
+
+def color_host(row_ptr, col_idx, is_boundary, new_to_old):
+    """lms_color_host: (colour by original id, number of colours)."""
+    rp, ci, b, p = (_arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8),
+                    _arr(new_to_old, np.int32))
+    n = len(rp) - 1
+    colour, nc = np.empty(n, np.int32), ctypes.c_int32()
+    _check(_lib().lms_color_host(n, _ptr(rp), _ptr(ci), _ptr(b), _ptr(p), _ptr(colour), ctypes.byref(nc)),
+           "lms_color_host")
+    return colour, nc.value
+
+
+def selftest_div64(s, d):
+    """Device quotients s/d by the FP64 sweep's division routine (lms_selftest_div64)."""
+    s, d = _arr(s, np.float64), _arr(d, np.int32)
+    q = np.empty_like(s)
+    _check(_lib().lms_selftest_div64(len(s), _ptr(s), _ptr(d), _ptr(q)), "lms_selftest_div64")
+    return q
+
+
+class Mesh:
+    """One mesh on the device (lms_handle)."""
+
+    def __init__(self, row_ptr, col_idx, xy, is_boundary, tri=None, precision=FP64, stream=None):
+        lib = _lib()
+        self.precision = PRECISIONS.get(precision, precision)
+        rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
+        self.n = len(rp) - 1
+        self.nnz = int(rp[-1])
+        xy = _host_f64(xy, self.n)
+        t = _arr(tri, np.int32) if tri is not None else None
+        self.ntri = 0 if t is None else t.size // 3
+        self.stream = current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(lib.lms_create(self.n, _ptr(rp), _ptr(ci), _ptr(xy), _ptr(b), self.ntri, _ptr(t), self.precision,
+                              ctypes.c_void_p(self.stream), ctypes.byref(h)), "lms_create")
+        self._h = h
+
+    @classmethod
+    def from_dict(cls, m, precision=FP64, stream=None):
+        return cls(m["row_ptr"], m["col_idx"], m["xy"], m["is_boundary"], m.get("tri"), precision, stream)
+
+    def _handle(self):
+        if self._h is None:
+            raise LmsError(-8, "Mesh", "handle closed")
+        return self._h
+
+    def reorder(self, ordering, seed=0):
+        _check(_lib().lms_reorder(self._handle(), ORDERINGS.get(ordering, ordering), seed & (2**64 - 1)),
+               "lms_reorder")
+
+    def smooth(self, iters, mode=JACOBI, tol=-1.0):
+        done = ctypes.c_int32()
+        _check(_lib().lms_smooth(self._handle(), int(iters), MODES.get(mode, mode), float(tol), ctypes.byref(done)),
+               "lms_smooth")
+        return done.value
+
+    def quality(self):
+        q = ctypes.c_double()
+        _check(_lib().lms_quality(self._handle(), ctypes.byref(q)), "lms_quality")
+        return q.value
+
+    def coords(self, out=None):
+        out = np.empty((self.n, 2), np.float64) if out is None else out
+        _check(_lib().lms_get_coords(self._handle(), _ptr(out)), "lms_get_coords")
+        return out
+
+    def set_coords(self, xy):
+        xy = _host_f64(xy, self.n)
+        _check(_lib().lms_set_coords(self._handle(), _ptr(xy)), "lms_set_coords")
+        self._keep = xy  # the copy is asynchronous for page-locked buffers
+
+    def permutation(self):
+        p = np.empty(self.n, np.int32)
+        _check(_lib().lms_get_permutation(self._handle(), _ptr(p)), "lms_get_permutation")
+        return p
+
+    def colors(self):
+        c, nc = np.empty(self.n, np.int32), ctypes.c_int32()
+        _check(_lib().lms_get_colors(self._handle(), _ptr(c), ctypes.byref(nc)), "lms_get_colors")
+        return c, nc.value
+
+    def csr(self):
+        rp, ci, p = np.empty(self.n + 1, np.int32), np.empty(max(1, self.nnz), np.int32), np.empty(self.n, np.int32)
+        _check(_lib().lms_get_csr(self._handle(), _ptr(rp), _ptr(ci), _ptr(p)), "lms_get_csr")
+        return rp, ci[: self.nnz], p
+
+    def last_stats(self):
+        d, ms, q0, q1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib().lms_last_stats(self._handle(), ctypes.byref(d), ctypes.byref(ms), ctypes.byref(q0),
+                                     ctypes.byref(q1)), "lms_last_stats")
+        return dict(max_disp=d.value, ms=ms.value, q_first=q0.value, q_last=q1.value)
+
+    def last_launches(self):
+        k = ctypes.c_int64()
+        _check(_lib().lms_last_launches(self._handle(), ctypes.byref(k)), "lms_last_launches")
+        return k.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib().lms_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent meshes smoothed by one persistent work-queue kernel per sweep (FP32)."""
+
+    def __init__(self, meshes, ordering=RDR, seed=0, stream=None):
+        lib = _lib()
+        self._keep = []
+        descs = (MeshDesc * len(meshes))()
+        self.sizes = []
+        for i, m in enumerate(meshes):
+            rp, ci = _arr(m["row_ptr"], np.int32), _arr(m["col_idx"], np.int32)
+            xy, b = _arr(m["xy"], np.float64), _arr(m["is_boundary"], np.uint8)
+            t = _arr(m["tri"], np.int32) if m.get("tri") is not None else None
+            self._keep.append((rp, ci, xy, b, t))
+            n = len(rp) - 1
+            self.sizes.append(n)
+            descs[i] = MeshDesc(n, _ptr(rp).value, _ptr(ci).value, _ptr(xy).value, _ptr(b).value,
+                                0 if t is None else t.size // 3, None if t is None else _ptr(t).value)
+        self.k = len(meshes)
+        self.stream = current_stream() if stream is None else int(stream)
+        h = ctypes.c_void_p()
+        _check(lib.lms_batch_create(self.k, descs, ORDERINGS.get(ordering, ordering), seed & (2**64 - 1),
+                                    ctypes.c_void_p(self.stream), ctypes.byref(h)), "lms_batch_create")
+        self._keep = None
+        self._h = h
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n_total = int(self.offsets[-1])
+
+    def _handle(self):
+        if self._h is None:
+            raise LmsError(-8, "Batch", "handle closed")
+        return self._h
+
+    def smooth(self, iters):
+        _check(_lib().lms_batch_smooth(self._handle(), int(iters)), "lms_batch_smooth")
+
+    def coords(self, mesh):
+        out = np.empty((self.sizes[mesh], 2), np.float64)
+        _check(_lib().lms_batch_get_coords(self._handle(), int(mesh), _ptr(out)), "lms_batch_get_coords")
+        return out
+
+    def all_coords(self, out=None):
+        out = np.empty((self.n_total, 2), np.float64) if out is None else out
+        _check(_lib().lms_batch_get_all_coords(self._handle(), _ptr(out)), "lms_batch_get_all_coords")
+        return out
+
+    def set_all_coords(self, xy):
+        xy = _host_f64(xy, self.n_total)
+        _check(_lib().lms_batch_set_all_coords(self._handle(), _ptr(xy)), "lms_batch_set_all_coords")
+        self._pending = xy
+
+    def permutation(self, mesh):
+        p = np.empty(self.sizes[mesh], np.int32)
+        _check(_lib().lms_batch_get_permutation(self._handle(), int(mesh), _ptr(p)), "lms_batch_get_permutation")
+        return p
+
+    def info(self):
+        n, ni, nnz, tiles = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib().lms_batch_info(self._handle(), ctypes.byref(n), ctypes.byref(ni), ctypes.byref(nnz),
+                                     ctypes.byref(tiles)), "lms_batch_info")
+        return dict(n_total=n.value, n_interior=ni.value, nnz_total=nnz.value, tiles=tiles.value)
+
+    def config(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(_lib().lms_batch_get_config(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_get_config")
+        return dict(block=v[0].value, lanes=v[1].value, tile=v[2].value, ctas_per_sm=v[3].value)
+
+    def set_config(self, block, lanes, tile, ctas_per_sm=0):
+        _check(_lib().lms_batch_set_config(self._handle(), block, lanes, tile, ctas_per_sm), "lms_batch_set_config")
+
+    def autotune(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(_lib().lms_batch_autotune(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_autotune")
+        return dict(block=v[0].value, lanes=v[1].value, tile=v[2].value, ctas_per_sm=v[3].value)
+
+    def last_launches(self):
+        k = ctypes.c_int64()
+        _check(_lib().lms_batch_last_launches(self._handle(), ctypes.byref(k)), "lms_batch_last_launches")
+        return k.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib().lms_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1270 @@
+// lms_capi.cpp - the C ABI of liblms (declared in include/lms.h): handles,
+// device memory, storage layouts, CUDA-graph capture of sweep loops, the
+// Section 5.1 stopping rule, the batched work-queue path and its autotuner.
+//
+// Storage layouts.  A handle keeps the mesh in one storage order at a time:
+//   - the ordering's layout (lms_reorder): position k holds original vertex
+//     new_to_old[k]; Jacobi sweeps run here;
+//   - the coloured layout (first LMS_COLORED_GS sweep after a reorder): the
+//     interior vertices sorted by (colour, position in the ordering), then the
+//     boundary vertices; each colour is one contiguous range, so one colour
+//     pass reads its rows and writes its positions contiguously, and its
+//     neighbour gathers stay inside the ordering's locality window of every
+//     other colour.  Jacobi results do not depend on the layout (rows keep
+//     their entry order), so Jacobi also runs on the coloured layout.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <thread>
+#include <vector>
+
+#include "lms_internal.h"
+
+using lms::DevState;
+using lms::SweepArgs;
+
+namespace {
+
+struct Allocator {
+    void* (*alloc)(size_t, void*, void*) = nullptr;
+    void (*release)(void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+#define LMS_CUDA(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            lms::set_error_detail(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? LMS_ERR_OOM : LMS_ERR_CUDA;                 \
+        }                                                                                        \
+    } while (0)
+
+#define LMS_TRY(expr)             \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != LMS_OK) return rc_; \
+    } while (0)
+
+// Device allocations of one handle, released together.
+struct Arena {
+    Allocator al;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> ptrs;
+
+    int get(void** out, size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        if (bytes == 0) bytes = 256;
+        void* p = nullptr;
+        if (al.alloc) {
+            p = al.alloc(bytes, stream, al.ctx);
+            if (!p) return LMS_ERR_OOM;
+        } else {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                lms::set_error_detail(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+                return LMS_ERR_OOM;
+            }
+        }
+        ptrs.push_back(p);
+        *out = p;
+        return LMS_OK;
+    }
+    template <typename T>
+    int get(T** out, size_t count) {
+        return get(reinterpret_cast<void**>(out), count * sizeof(T));
+    }
+    void release_all() {
+        for (void* p : ptrs) {
+            if (al.release)
+                al.release(p, al.ctx);
+            else
+                cudaFree(p);
+        }
+        ptrs.clear();
+    }
+};
+
+struct GraphCache {
+    std::map<std::string, cudaGraphExec_t> execs;
+    std::map<std::string, int64_t> kernels;
+    void clear() {
+        for (auto& kv : execs) cudaGraphExecDestroy(kv.second);
+        execs.clear();
+        kernels.clear();
+    }
+};
+
+int64_t count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// Record `body` (issuing work on the capture stream) into an executable graph.
+template <typename F>
+int capture(cudaStream_t cap, F&& body, cudaGraphExec_t* exec, int64_t* kernels) {
+    LMS_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    int rc = body(cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (rc != LMS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    *kernels = count_kernel_nodes(g);
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    return LMS_OK;
+}
+
+int check_launch(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LMS_OK;
+    lms::set_error_detail(std::string(what) + ": " + cudaGetErrorString(e));
+    return LMS_ERR_CUDA;
+}
+
+bool all_finite(const double* xy, int64_t count) {
+    for (int64_t i = 0; i < count; ++i)
+        if (!std::isfinite(xy[i])) return false;
+    return true;
+}
+
+// Bounding box centre and scale (the larger side; 1 for a degenerate box).
+void bbox(const double* xy, int32_t n, double* cx, double* cy, double* s) {
+    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+    for (int32_t v = 1; v < n; ++v) {
+        x0 = std::min(x0, xy[2 * v]);
+        x1 = std::max(x1, xy[2 * v]);
+        y0 = std::min(y0, xy[2 * v + 1]);
+        y1 = std::max(y1, xy[2 * v + 1]);
+    }
+    *cx = 0.5 * (x0 + x1);
+    *cy = 0.5 * (y0 + y1);
+    double side = std::max(x1 - x0, y1 - y0);
+    *s = side > 0.0 ? side : 1.0;
+}
+
+// Vertex -> triangle incidence, rows in ascending triangle id.
+void build_incidence(int32_t n, int32_t ntri, const int32_t* tri, std::vector<int32_t>& ptr,
+                     std::vector<int32_t>& idx) {
+    ptr.assign(n + 1, 0);
+    for (int64_t i = 0; i < 3 * int64_t(ntri); ++i) ptr[tri[i] + 1]++;
+    for (int32_t v = 0; v < n; ++v) ptr[v + 1] += ptr[v];
+    idx.resize(std::max<int64_t>(1, 3 * int64_t(ntri)));
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int32_t t = 0; t < ntri; ++t)
+        for (int c = 0; c < 3; ++c) idx[fill[tri[3 * t + c]]++] = t;
+}
+
+// w_t = sum over t's corners of 1 / (number of triangles at the corner)
+void build_weights(int32_t ntri, const int32_t* tri, const std::vector<int32_t>& ptr, std::vector<double>& w) {
+    w.resize(std::max<int32_t>(1, ntri));
+    for (int32_t t = 0; t < ntri; ++t) {
+        double s = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            int32_t v = tri[3 * t + c];
+            s += 1.0 / double(ptr[v + 1] - ptr[v]);
+        }
+        w[t] = s;
+    }
+}
+
+std::vector<double> recip_table() {
+    std::vector<double> r(lms::kMaxRecipDeg + 1, 0.0);
+    for (int d = 1; d <= lms::kMaxRecipDeg; ++d) r[d] = 1.0 / double(d);
+    return r;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct lms_mesh_s {
+    Arena arena;
+    cudaStream_t stream = nullptr;      // caller's stream (work runs here)
+    cudaStream_t cap = nullptr;         // private stream used only to record graphs
+    int precision = LMS_FP64;
+    int32_t n = 0, ntri = 0, nnz = 0;
+    // host copies, original labelling
+    std::vector<int32_t> rp, ci, tri;
+    std::vector<uint8_t> bnd;
+    // orderings
+    std::vector<int32_t> user_perm;     // the ordering (new_to_old)
+    std::vector<int32_t> perm;          // current storage layout (new_to_old)
+    bool coloured_layout = false;
+    bool colours_valid = false;
+    std::vector<int32_t> colour;        // by original id
+    int32_t ncolours = 0;
+    std::vector<int32_t> colour_ofs;    // colour c occupies storage [ofs[c], ofs[c+1])
+    double cx = 0, cy = 0, scale = 1;   // FP32 normalisation
+    // device, original labelling
+    int32_t *d_rp0 = nullptr, *d_ci0 = nullptr, *d_tri0 = nullptr, *d_vt_ptr = nullptr, *d_vt_idx = nullptr;
+    uint8_t* d_bnd0 = nullptr;
+    double* d_w = nullptr;
+    // device, current layout
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_tri = nullptr, *d_perm = nullptr, *d_tmp = nullptr;
+    uint32_t* d_bits = nullptr;
+    void* d_xy[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* d_xy_swap = nullptr;          // layout changes
+    double* d_xy64 = nullptr;           // FP64 staging in original order (input / output / RDR keys)
+    double* d_pristine = nullptr;       // FP32: caller's last coordinates, original order (boundary rows
+                                        // stay valid after sweeps: boundary vertices never move)
+    bool pristine_valid = false;
+    double *d_qt = nullptr, *d_qv = nullptr, *d_partials = nullptr, *d_recip = nullptr;
+    DevState* d_state = nullptr;
+    DevState* h_state = nullptr;        // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    GraphCache graphs;
+    int64_t last_launches = 0;
+    bool stats_pending = false;
+    int last_disp_slot = 0;
+    double last_disp = NAN, last_ms = NAN, q_first = NAN, q_last = NAN;
+
+    ~lms_mesh_s() {
+        if (stream) cudaStreamSynchronize(stream);
+        graphs.clear();
+        arena.release_all();
+        if (h_state) cudaFreeHost(h_state);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+// Move the mesh to storage order `perm_new` (new_to_old): CSR rows gathered from the original
+// ones with ids mapped, triangles mapped, boundary bits, positions carried over.
+int apply_layout(lms_mesh_s* h, const std::vector<int32_t>& perm_new) {
+    const int32_t n = h->n;
+    std::vector<int32_t> old_inv(n), rel(n), new_inv(n), rp(n + 1);
+    for (int32_t k = 0; k < n; ++k) old_inv[h->perm[k]] = k;
+    for (int32_t k = 0; k < n; ++k) {
+        rel[k] = old_inv[perm_new[k]];
+        new_inv[perm_new[k]] = k;
+    }
+    rp[0] = 0;
+    for (int32_t k = 0; k < n; ++k) rp[k + 1] = rp[k] + (h->rp[perm_new[k] + 1] - h->rp[perm_new[k]]);
+    cudaStream_t s = h->stream;
+    LMS_CUDA(cudaMemcpyAsync(h->d_perm, perm_new.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    LMS_CUDA(cudaMemcpyAsync(h->d_tmp, new_inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    LMS_CUDA(cudaMemcpyAsync(h->d_rp, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    LMS_TRY(check_launch(lms::launch_gather_rows(n, h->d_perm, h->d_rp0, h->d_ci0, h->d_rp, h->d_ci, h->d_tmp, s),
+                         "gather_rows"));
+    if (h->ntri > 0)
+        LMS_TRY(check_launch(lms::launch_map_ids(3 * int64_t(h->ntri), h->d_tmp, h->d_tri0, h->d_tri, s), "map_ids"));
+    LMS_TRY(check_launch(lms::launch_boundary_bits(n, h->d_perm, h->d_bnd0, h->d_bits, s), "boundary_bits"));
+    // positions: swap <- cur[rel], then both ping-pong buffers <- swap
+    LMS_CUDA(cudaMemcpyAsync(h->d_tmp, rel.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    LMS_TRY(check_launch(lms::launch_gather_xy(h->precision, n, h->d_tmp, h->d_xy[h->cur], h->d_xy_swap, s),
+                         "gather_xy"));
+    const size_t vb = (h->precision == LMS_FP64 ? 16 : 8) * size_t(n);
+    LMS_CUDA(cudaMemcpyAsync(h->d_xy[0], h->d_xy_swap, vb, cudaMemcpyDeviceToDevice, s));
+    LMS_CUDA(cudaMemcpyAsync(h->d_xy[1], h->d_xy_swap, vb, cudaMemcpyDeviceToDevice, s));
+    h->cur = 0;
+    // the host vectors above must outlive the asynchronous copies
+    LMS_CUDA(cudaStreamSynchronize(s));
+    h->perm = perm_new;
+    h->graphs.clear();
+    return LMS_OK;
+}
+
+// Current positions as FP64 in the original labelling, in d_xy64.
+int positions_fp64_original(lms_mesh_s* h) {
+    if (h->precision == LMS_FP32 && h->pristine_valid) {
+        LMS_CUDA(cudaMemcpyAsync(h->d_xy64, h->d_pristine, 16 * size_t(h->n), cudaMemcpyDeviceToDevice, h->stream));
+        return LMS_OK;
+    }
+    return check_launch(lms::launch_store_xy(h->precision, h->n, h->d_perm, h->d_xy[h->cur], h->d_xy64, h->cx,
+                                             h->cy, h->scale, h->d_bnd0, h->d_pristine, h->stream),
+                        "store_xy");
+}
+
+int ensure_colours(lms_mesh_s* h) {
+    if (h->colours_valid) return LMS_OK;
+    h->colour.assign(h->n, -1);
+    LMS_TRY(lms::colour_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), h->user_perm.data(),
+                                 h->colour.data(), &h->ncolours));
+    h->colours_valid = true;
+    return LMS_OK;
+}
+
+int ensure_coloured_layout(lms_mesh_s* h) {
+    if (h->coloured_layout) return LMS_OK;
+    LMS_TRY(ensure_colours(h));
+    const int32_t n = h->n, nc = h->ncolours;
+    h->colour_ofs.assign(nc + 1, 0);
+    for (int32_t v = 0; v < n; ++v)
+        if (h->colour[v] >= 0) h->colour_ofs[h->colour[v] + 1]++;
+    for (int32_t c = 0; c < nc; ++c) h->colour_ofs[c + 1] += h->colour_ofs[c];
+    std::vector<int32_t> fill(h->colour_ofs.begin(), h->colour_ofs.end());
+    std::vector<int32_t> p(n);
+    int32_t tail = h->colour_ofs[nc];
+    for (int32_t k = 0; k < n; ++k) {  // stable in the ordering's position
+        int32_t v = h->user_perm[k];
+        int32_t c = h->colour[v];
+        if (c >= 0)
+            p[fill[c]++] = v;
+        else
+            p[tail++] = v;
+    }
+    LMS_TRY(apply_layout(h, p));
+    h->coloured_layout = true;
+    return LMS_OK;
+}
+
+SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
+    SweepArgs a{};
+    a.row_ptr = h->d_rp;
+    a.col_idx = h->d_ci;
+    a.bnd_bits = h->d_bits;
+    a.src = h->d_xy[src];
+    a.dst = h->d_xy[dst];
+    a.v_begin = 0;
+    a.v_end = h->n;
+    a.recip = h->d_recip;
+    return a;
+}
+
+// One sweep issued on stream s.  k1 = 1-based sweep index (selects the displacement slot);
+// base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
+int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
+    const int src = (base + k1 - 1) & 1;
+    if (mode == LMS_JACOBI) {
+        SweepArgs a = sweep_args(h, src, src ^ 1);
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        return check_launch(lms::launch_sweep(h->precision, false, a, 256, s), "sweep");
+    }
+    for (int32_t c = 0; c < h->ncolours; ++c) {
+        SweepArgs a = sweep_args(h, base, base);
+        a.bnd_bits = nullptr;  // every vertex of a colour range is interior
+        a.v_begin = h->colour_ofs[c];
+        a.v_end = h->colour_ofs[c + 1];
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, 256, s), "sweep"));
+    }
+    return LMS_OK;
+}
+
+int get_graph(lms_mesh_s* h, const std::string& key, const std::function<int(cudaStream_t)>& body,
+              cudaGraphExec_t* exec, int64_t* kernels) {
+    auto it = h->graphs.execs.find(key);
+    if (it != h->graphs.execs.end()) {
+        *exec = it->second;
+        *kernels = h->graphs.kernels[key];
+        return LMS_OK;
+    }
+    LMS_TRY(capture(h->cap, body, exec, kernels));
+    h->graphs.execs[key] = *exec;
+    h->graphs.kernels[key] = *kernels;
+    return LMS_OK;
+}
+
+int finish_stats(lms_mesh_s* h) {
+    if (!h->stats_pending) return LMS_OK;
+    LMS_CUDA(cudaStreamSynchronize(h->stream));
+    DevState st;
+    LMS_CUDA(cudaMemcpy(&st, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost));
+    double d2 = 0.0;
+    std::memcpy(&d2, &st.disp2[h->last_disp_slot], sizeof(double));
+    h->last_disp = std::sqrt(d2) * (h->precision == LMS_FP32 ? h->scale : 1.0);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last_ms = ms;
+    if (st.err != 0) {
+        h->stats_pending = false;
+        return LMS_ERR_TIMEOUT;
+    }
+    h->stats_pending = false;
+    return LMS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int lms_set_device_allocator(void* (*alloc)(size_t, void*, void*), void (*release)(void*, void*), void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return LMS_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = ctx;
+    return LMS_OK;
+}
+
+int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* xy,
+               const uint8_t* is_boundary, int32_t ntri, const int32_t* tri, int precision, void* cuda_stream,
+               lms_handle* out) {
+    if (!out || !xy || (precision != LMS_FP64 && precision != LMS_FP32)) return LMS_ERR_ARG;
+    *out = nullptr;
+    LMS_TRY(lms::validate_mesh(n, row_ptr, col_idx, is_boundary, ntri, tri));
+    if (!all_finite(xy, 2 * int64_t(n))) return LMS_ERR_ARG;
+
+    auto h = new (std::nothrow) lms_mesh_s();
+    if (!h) return LMS_ERR_OOM;
+    auto fail = [&](int rc) {
+        delete h;
+        return rc;
+    };
+    {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        h->arena.al = g_alloc;
+    }
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->arena.stream = h->stream;
+    h->precision = precision;
+    h->n = n;
+    h->ntri = ntri;
+    h->nnz = row_ptr[n];
+    h->rp.assign(row_ptr, row_ptr + n + 1);
+    h->ci.assign(col_idx, col_idx + h->nnz);
+    h->bnd.assign(is_boundary, is_boundary + n);
+    for (auto& b : h->bnd) b = b ? 1 : 0;
+    if (ntri > 0) h->tri.assign(tri, tri + 3 * int64_t(ntri));
+    h->user_perm.resize(n);
+    for (int32_t i = 0; i < n; ++i) h->user_perm[i] = i;
+    h->perm = h->user_perm;
+    bbox(xy, n, &h->cx, &h->cy, &h->scale);
+
+    std::vector<int32_t> vt_ptr, vt_idx;
+    std::vector<double> w;
+    build_incidence(n, ntri, h->tri.data(), vt_ptr, vt_idx);
+    build_weights(ntri, h->tri.data(), vt_ptr, w);
+
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        return fail(LMS_ERR_CUDA);
+    }
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&h->h_state), sizeof(DevState)) != cudaSuccess)
+        return fail(LMS_ERR_CUDA);
+
+    Arena& A = h->arena;
+    const size_t vb = (precision == LMS_FP64 ? 16 : 8) * size_t(n);
+    const int64_t t3 = std::max<int64_t>(1, 3 * int64_t(ntri));
+    int rc = LMS_OK;
+    if ((rc = A.get(&h->d_rp0, n + 1)) || (rc = A.get(&h->d_ci0, std::max(1, h->nnz))) ||
+        (rc = A.get(&h->d_tri0, t3)) || (rc = A.get(&h->d_vt_ptr, n + 1)) || (rc = A.get(&h->d_vt_idx, t3)) ||
+        (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1)) ||
+        (rc = A.get(&h->d_ci, std::max(1, h->nnz))) || (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
+        (rc = A.get(&h->d_tmp, n)) || (rc = A.get(&h->d_bits, (n + 31) / 32 + 4)) ||
+        (rc = A.get(&h->d_xy[0], vb)) || (rc = A.get(&h->d_xy[1], vb)) || (rc = A.get(&h->d_xy_swap, vb)) ||
+        (rc = A.get(&h->d_xy64, 2 * size_t(n))) || (rc = A.get(&h->d_qt, std::max(1, ntri))) ||
+        (rc = A.get(&h->d_qv, n)) || (rc = A.get(&h->d_partials, lms::kQualityBlocks)) ||
+        (rc = A.get(&h->d_recip, lms::kMaxRecipDeg + 1)) || (rc = A.get(&h->d_state, 1)))
+        return fail(rc);
+    if (precision == LMS_FP32 && (rc = A.get(&h->d_pristine, 2 * size_t(n)))) return fail(rc);
+
+    cudaStream_t s = h->stream;
+    auto recip = recip_table();
+    std::vector<int32_t> ident(n);
+    for (int32_t i = 0; i < n; ++i) ident[i] = i;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    if (up(h->d_rp0, h->rp.data(), 4 * size_t(n + 1)) || up(h->d_ci0, h->ci.data(), 4 * size_t(h->nnz)) ||
+        up(h->d_tri0, h->tri.data(), 12 * size_t(ntri)) || up(h->d_vt_ptr, vt_ptr.data(), 4 * size_t(n + 1)) ||
+        up(h->d_vt_idx, vt_idx.data(), 12 * size_t(ntri)) || up(h->d_bnd0, h->bnd.data(), size_t(n)) ||
+        up(h->d_w, w.data(), 8 * size_t(ntri)) || up(h->d_recip, recip.data(), 8 * recip.size()) ||
+        up(h->d_perm, ident.data(), 4 * size_t(n)) || up(h->d_rp, h->rp.data(), 4 * size_t(n + 1)) ||
+        up(h->d_ci, h->ci.data(), 4 * size_t(h->nnz)) || up(h->d_tri, h->tri.data(), 12 * size_t(ntri)) ||
+        up(h->d_xy64, xy, 16 * size_t(n)) || cudaMemsetAsync(h->d_state, 0, sizeof(DevState), s)) {
+        lms::set_error_detail(std::string("upload: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(LMS_ERR_CUDA);
+    }
+    if ((rc = check_launch(lms::launch_boundary_bits(n, h->d_perm, h->d_bnd0, h->d_bits, s), "boundary_bits")))
+        return fail(rc);
+    const double inv_s = 1.0 / h->scale;
+    for (int b = 0; b < 2; ++b)
+        if ((rc = check_launch(lms::launch_load_xy(precision, n, h->d_perm, h->d_xy64, h->d_xy[b], h->cx, h->cy,
+                                                   inv_s, s),
+                               "load_xy")))
+            return fail(rc);
+    if (precision == LMS_FP32) {
+        if (cudaMemcpyAsync(h->d_pristine, h->d_xy64, 16 * size_t(n), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(LMS_ERR_CUDA);
+        h->pristine_valid = true;
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("create: ") + cudaGetErrorString(e));
+        return fail(LMS_ERR_CUDA);
+    }
+    *out = h;
+    return LMS_OK;
+}
+
+int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
+    if (!h || ordering < LMS_ORI || ordering > LMS_RDR) return LMS_ERR_ARG;
+    if (ordering == LMS_RDR && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
+    LMS_TRY(finish_stats(h));
+    std::vector<double> q;
+    if (ordering == LMS_RDR) {
+        // keys: Section 3.2 vertex qualities of the current positions, FP64, original labels
+        LMS_TRY(positions_fp64_original(h));
+        LMS_TRY(check_launch(lms::launch_tri_quality_exact(h->ntri, h->d_tri0, h->d_xy64, h->d_qt, h->stream),
+                             "tri_quality"));
+        LMS_TRY(check_launch(
+            lms::launch_vertex_quality_exact(h->n, h->d_vt_ptr, h->d_vt_idx, h->d_qt, h->d_qv, h->stream),
+            "vertex_quality"));
+        q.resize(h->n);
+        LMS_CUDA(cudaMemcpyAsync(q.data(), h->d_qv, 8 * size_t(h->n), cudaMemcpyDeviceToHost, h->stream));
+        LMS_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    std::vector<int32_t> p(h->n);
+    LMS_TRY(lms::order_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), q.empty() ? nullptr : q.data(),
+                                ordering, seed, p.data()));
+    h->user_perm = p;
+    h->colours_valid = false;
+    h->coloured_layout = false;
+    return apply_layout(h, p);
+}
+
+int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done) {
+    if (!h || max_iters < 0 || (mode != LMS_JACOBI && mode != LMS_COLORED_GS) || std::isnan(tol)) return LMS_ERR_ARG;
+    if (tol >= 0.0 && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
+    LMS_TRY(finish_stats(h));
+    if (mode == LMS_COLORED_GS) LMS_TRY(ensure_coloured_layout(h));
+    if (iters_done) *iters_done = 0;
+    h->q_first = h->q_last = NAN;
+    h->last_disp = NAN;
+    if (max_iters == 0) return LMS_OK;
+    cudaStream_t s = h->stream;
+    const int base = h->cur;
+    const double nd = double(h->n);
+
+    if (tol < 0.0) {
+        std::string key = "fixed/" + std::to_string(mode) + "/" + std::to_string(max_iters) + "/" + std::to_string(base);
+        cudaGraphExec_t exec;
+        int64_t kernels = 0;
+        LMS_TRY(get_graph(h, key,
+                          [&](cudaStream_t cs) -> int {
+                              LMS_CUDA(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), cs));
+                              for (int32_t k = 1; k <= max_iters; ++k)
+                                  LMS_TRY(issue_sweep(h, mode, base, k, k == max_iters, false, cs));
+                              return LMS_OK;
+                          },
+                          &exec, &kernels));
+        LMS_CUDA(cudaEventRecord(h->ev0, s));
+        LMS_CUDA(cudaGraphLaunch(exec, s));
+        LMS_CUDA(cudaEventRecord(h->ev1, s));
+        h->last_launches = kernels;
+        h->last_disp_slot = max_iters & 1;
+        h->stats_pending = true;
+        if (mode == LMS_JACOBI) h->cur = (base + max_iters) & 1;
+        h->pristine_valid = false;
+        if (iters_done) *iters_done = max_iters;
+        return LMS_OK;
+    }
+
+    // Algorithm 1 with the Section 5.1 rule: Q_0, then chunks of sweeps each followed by the
+    // quality reduction and the stop check, replayed from one graph until the rule fires.
+    constexpr int32_t kChunk = 8;
+    DevState init{};
+    *h->h_state = init;
+    LMS_CUDA(cudaEventRecord(h->ev0, s));
+    LMS_CUDA(cudaMemcpyAsync(h->d_state, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    LMS_TRY(check_launch(lms::launch_quality_partials(h->precision, h->ntri, h->d_tri, h->d_xy[base], h->d_w,
+                                                      h->d_partials, nullptr, s),
+                         "quality"));
+    LMS_TRY(check_launch(lms::launch_quality_finish(h->d_partials, nd, h->d_state, 1, s), "quality_finish"));
+    int64_t launches = 2;
+    char tol_hex[64];
+    std::snprintf(tol_hex, sizeof(tol_hex), "%a", tol);
+    std::string key = "stop/" + std::to_string(mode) + "/" + std::to_string(base) + "/" + std::to_string(max_iters) +
+                      "/" + tol_hex;
+    cudaGraphExec_t exec;
+    int64_t kernels = 0;
+    LMS_TRY(get_graph(h, key,
+                      [&](cudaStream_t cs) -> int {
+                          for (int32_t i = 0; i < kChunk; ++i) {
+                              const int k1 = 1 + i;  // chunks start at odd sweep indices (kChunk is even)
+                              LMS_TRY(issue_sweep(h, mode, base, k1, true, true, cs));
+                              const void* xy = h->d_xy[mode == LMS_JACOBI ? ((base + k1) & 1) : base];
+                              LMS_TRY(check_launch(lms::launch_quality_partials(h->precision, h->ntri, h->d_tri, xy,
+                                                                                h->d_w, h->d_partials, h->d_state, cs),
+                                                   "quality"));
+                              LMS_TRY(check_launch(lms::launch_stop_check(h->d_partials, nd, h->d_state, tol,
+                                                                          INFINITY, max_iters, cs),
+                                                   "stop_check"));
+                          }
+                          return LMS_OK;
+                      },
+                      &exec, &kernels));
+    int32_t done = 0;
+    for (int32_t launched = 0; launched < max_iters; launched += kChunk) {
+        LMS_CUDA(cudaGraphLaunch(exec, s));
+        launches += kernels;
+        LMS_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        LMS_CUDA(cudaStreamSynchronize(s));
+        if (h->h_state->stop) {
+            done = h->h_state->iters_at_stop;
+            break;
+        }
+    }
+    LMS_CUDA(cudaEventRecord(h->ev1, s));
+    LMS_CUDA(cudaStreamSynchronize(s));
+    if (h->h_state->err) return LMS_ERR_TIMEOUT;
+    if (!h->h_state->stop) {
+        lms::set_error_detail("stopping rule did not terminate within max_iters");
+        return LMS_ERR_STATE;
+    }
+    h->last_launches = launches;
+    h->q_first = h->h_state->q_first;
+    h->q_last = h->h_state->q_cur;
+    h->last_disp_slot = done & 1;
+    h->stats_pending = true;
+    if (mode == LMS_JACOBI) h->cur = (base + done) & 1;
+    h->pristine_valid = false;
+    if (iters_done) *iters_done = done;
+    return finish_stats(h);
+}
+
+int lms_quality(lms_handle h, double* Q) {
+    if (!h || !Q) return LMS_ERR_ARG;
+    if (h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
+    LMS_TRY(finish_stats(h));
+    cudaStream_t s = h->stream;
+    LMS_TRY(check_launch(lms::launch_quality_partials(h->precision, h->ntri, h->d_tri, h->d_xy[h->cur], h->d_w,
+                                                      h->d_partials, nullptr, s),
+                         "quality"));
+    LMS_TRY(check_launch(lms::launch_quality_finish(h->d_partials, double(h->n), h->d_state, 0, s), "quality_finish"));
+    LMS_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LMS_CUDA(cudaStreamSynchronize(s));
+    *Q = h->h_state->q_cur;
+    return LMS_OK;
+}
+
+int lms_get_coords(lms_handle h, double* xy) {
+    if (!h || !xy) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    LMS_TRY(positions_fp64_original(h));
+    LMS_CUDA(cudaMemcpyAsync(xy, h->d_xy64, 16 * size_t(h->n), cudaMemcpyDeviceToHost, h->stream));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));
+    return LMS_OK;
+}
+
+int lms_set_coords(lms_handle h, const double* xy) {
+    if (!h || !xy) return LMS_ERR_ARG;
+    if (!all_finite(xy, 2 * int64_t(h->n))) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    cudaStream_t s = h->stream;
+    LMS_CUDA(cudaMemcpyAsync(h->d_xy64, xy, 16 * size_t(h->n), cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < 2; ++b)
+        LMS_TRY(check_launch(lms::launch_load_xy(h->precision, h->n, h->d_perm, h->d_xy64, h->d_xy[b], h->cx, h->cy,
+                                                 1.0 / h->scale, s),
+                             "load_xy"));
+    if (h->precision == LMS_FP32) {
+        LMS_CUDA(cudaMemcpyAsync(h->d_pristine, h->d_xy64, 16 * size_t(h->n), cudaMemcpyDeviceToDevice, s));
+        h->pristine_valid = true;
+    }
+    h->cur = 0;
+    return LMS_OK;
+}
+
+int lms_get_permutation(lms_handle h, int32_t* new_to_old) {
+    if (!h || !new_to_old) return LMS_ERR_ARG;
+    std::memcpy(new_to_old, h->user_perm.data(), sizeof(int32_t) * h->n);
+    return LMS_OK;
+}
+
+int lms_get_colors(lms_handle h, int32_t* colour, int32_t* ncolours) {
+    if (!h || !colour || !ncolours) return LMS_ERR_ARG;
+    LMS_TRY(ensure_colours(h));
+    std::memcpy(colour, h->colour.data(), sizeof(int32_t) * h->n);
+    *ncolours = h->ncolours;
+    return LMS_OK;
+}
+
+int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx, int32_t* storage_new_to_old) {
+    if (!h || !row_ptr || (!col_idx && h->nnz > 0)) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    LMS_CUDA(cudaMemcpyAsync(row_ptr, h->d_rp, 4 * size_t(h->n + 1), cudaMemcpyDeviceToHost, h->stream));
+    if (h->nnz > 0)
+        LMS_CUDA(cudaMemcpyAsync(col_idx, h->d_ci, 4 * size_t(h->nnz), cudaMemcpyDeviceToHost, h->stream));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));
+    if (storage_new_to_old) std::memcpy(storage_new_to_old, h->perm.data(), sizeof(int32_t) * h->n);
+    return LMS_OK;
+}
+
+int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, double* q_last) {
+    if (!h) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    if (max_disp) *max_disp = h->last_disp;
+    if (ms) *ms = h->last_ms;
+    if (q_first) *q_first = h->q_first;
+    if (q_last) *q_last = h->q_last;
+    return LMS_OK;
+}
+
+int lms_last_launches(lms_handle h, int64_t* launches) {
+    if (!h || !launches) return LMS_ERR_ARG;
+    *launches = h->last_launches;
+    return LMS_OK;
+}
+
+int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q) {
+    if (count < 0 || (count > 0 && (!s || !d || !q))) return LMS_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (d[i] < 1) return LMS_ERR_ARG;
+    if (count == 0) return LMS_OK;
+    Arena A;
+    double *ds = nullptr, *dq = nullptr, *dr = nullptr;
+    int32_t* dd = nullptr;
+    int rc = LMS_OK;
+    if ((rc = A.get(&ds, count)) || (rc = A.get(&dq, count)) || (rc = A.get(&dr, lms::kMaxRecipDeg + 1)) ||
+        (rc = A.get(&dd, count))) {
+        A.release_all();
+        return rc;
+    }
+    auto recip = recip_table();
+    cudaError_t e = cudaMemcpy(ds, s, 8 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, d, 4 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dr, recip.data(), 8 * recip.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = lms::launch_div_selftest(count, ds, dd, dr, dq, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(q, dq, 8 * size_t(count), cudaMemcpyDeviceToHost);
+    A.release_all();
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("selftest: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    return LMS_OK;
+}
+
+const char* lms_last_error_detail(void) { return lms::error_detail().c_str(); }
+
+void lms_destroy(lms_handle h) { delete h; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+
+struct lms_batch_s {
+    Arena arena;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    int32_t k = 0;
+    int64_t n_total = 0, n_int = 0, nnz_total = 0;
+    std::vector<int64_t> voff;          // vertex offset of each mesh (k+1)
+    std::vector<int32_t> perm;          // global new_to_old
+    std::vector<double> cs;             // per mesh (cx, cy, inv_s, s)
+    int32_t *d_rp = nullptr, *d_ci = nullptr, *d_perm = nullptr, *d_item_mesh = nullptr, *d_queue = nullptr;
+    uint32_t* d_bits = nullptr;
+    int2* d_items = nullptr;
+    float2* d_xy[3] = {nullptr, nullptr, nullptr};  // ping-pong + autotune scratch
+    double* d_xy64 = nullptr;           // FP64 staging, original order
+    double* d_fixed = nullptr;          // caller's last coordinates, original order (boundary values)
+    double* d_cs = nullptr;
+    int cur = 0;
+    int32_t queue_slots = 0;
+    // launch configuration
+    int block = 256, lanes = 1, tile = 1024, ctas_per_sm = 0;
+    bool configured = false;
+    int32_t n_items = 0;
+    int items_tile = 0;                 // tile size the item table was built for
+    int2* d_items_cap = nullptr;
+    int32_t* d_item_mesh_cap = nullptr;
+    int64_t items_capacity = 0;
+    GraphCache graphs;
+    int64_t last_launches = 0;
+    int sms = 0;
+
+    ~lms_batch_s() {
+        if (stream) cudaStreamSynchronize(stream);
+        graphs.clear();
+        arena.release_all();
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+int batch_build_items(lms_batch_s* b, int tile) {
+    if (b->items_tile == tile) return LMS_OK;
+    std::vector<int2> items;
+    std::vector<int32_t> im;
+    for (int32_t m = 0; m < b->k; ++m)
+        for (int64_t v = b->voff[m]; v < b->voff[m + 1]; v += tile) {
+            items.push_back(make_int2(int32_t(v), int32_t(std::min<int64_t>(v + tile, b->voff[m + 1]))));
+            im.push_back(m);
+        }
+    if (int64_t(items.size()) > b->items_capacity) return LMS_ERR_STATE;
+    LMS_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaMemcpyAsync(b->d_item_mesh, im.data(), sizeof(int32_t) * im.size(), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    b->n_items = int32_t(items.size());
+    b->items_tile = tile;
+    b->graphs.clear();
+    return LMS_OK;
+}
+
+SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
+    SweepArgs a{};
+    a.row_ptr = b->d_rp;
+    a.col_idx = b->d_ci;
+    a.bnd_bits = b->d_bits;
+    a.src = b->d_xy[src];
+    a.dst = b->d_xy[dst];
+    a.items = b->d_items;
+    a.n_items = b->n_items;
+    a.queue = b->d_queue + slot;
+    return a;
+}
+
+int batch_grid(lms_batch_s* b) {
+    int occ = lms::batch_sweep_occupancy(b->block, b->lanes);
+    if (occ <= 0) occ = 1;
+    int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+    return std::max(1, per_sm * b->sms);
+}
+
+int ensure_queue(lms_batch_s* b, int32_t slots) {
+    if (slots <= b->queue_slots) return LMS_OK;
+    int32_t want = std::max<int32_t>(slots, 64);
+    LMS_TRY(b->arena.get(&b->d_queue, want));
+    b->queue_slots = want;
+    b->graphs.clear();
+    return LMS_OK;
+}
+
+std::string autotune_key(lms_batch_s* b) {
+    cudaDeviceProp p;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&p, dev);
+    auto bucket = [](int64_t x) {
+        int l = 0;
+        while (x > 1) {
+            x >>= 1;
+            ++l;
+        }
+        return l;
+    };
+    std::ostringstream os;
+    os << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    std::string s = os.str();
+    for (auto& c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint64_t seed, void* cuda_stream,
+                     lms_batch* out) {
+    if (!out || !meshes || k <= 0 || ordering < LMS_ORI || ordering > LMS_RDR) return LMS_ERR_ARG;
+    *out = nullptr;
+    // validate in parallel
+    std::vector<int> status(k, LMS_OK);
+    {
+        std::atomic<int32_t> next(0);
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < nt; ++t)
+            pool.emplace_back([&]() {
+                for (int32_t m; (m = next++) < k;) {
+                    const lms_mesh_desc& d = meshes[m];
+                    int rc = lms::validate_mesh(d.n, d.row_ptr, d.col_idx, d.is_boundary, d.ntri, d.tri);
+                    if (rc == LMS_OK && (!d.xy || !all_finite(d.xy, 2 * int64_t(d.n)))) rc = LMS_ERR_ARG;
+                    if (rc == LMS_OK && ordering == LMS_RDR && (d.ntri <= 0 || !d.tri)) rc = LMS_ERR_NO_TRIANGLES;
+                    status[m] = rc;
+                }
+            });
+        for (auto& th : pool) th.join();
+    }
+    for (int rc : status)
+        if (rc != LMS_OK) return rc;
+
+    auto b = new (std::nothrow) lms_batch_s();
+    if (!b) return LMS_ERR_OOM;
+    auto fail = [&](int rc) {
+        delete b;
+        return rc;
+    };
+    {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        b->arena.al = g_alloc;
+    }
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->arena.stream = b->stream;
+    b->k = k;
+    b->voff.assign(k + 1, 0);
+    std::vector<int64_t> eoff(k + 1, 0), toff(k + 1, 0);
+    for (int32_t m = 0; m < k; ++m) {
+        b->voff[m + 1] = b->voff[m] + meshes[m].n;
+        eoff[m + 1] = eoff[m] + meshes[m].row_ptr[meshes[m].n];
+        toff[m + 1] = toff[m] + (ordering == LMS_RDR ? meshes[m].ntri : 0);
+        for (int32_t v = 0; v < meshes[m].n; ++v) b->n_int += meshes[m].is_boundary[v] ? 0 : 1;
+    }
+    b->n_total = b->voff[k];
+    b->nnz_total = eoff[k];
+    if (b->n_total >= INT32_MAX || b->nnz_total >= INT32_MAX || toff[k] * 3 >= INT32_MAX) return fail(LMS_ERR_ARG);
+    const int32_t N = int32_t(b->n_total), E = int32_t(b->nnz_total), T = int32_t(toff[k]);
+    cudaDeviceProp prop;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return fail(LMS_ERR_CUDA);
+    b->sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(LMS_ERR_CUDA);
+
+    // concatenated original arrays (global ids)
+    std::vector<int32_t> rp0(N + 1), ci0(std::max(1, E)), tri0(std::max<int64_t>(3, 3 * int64_t(T)));
+    std::vector<uint8_t> bnd0(N);
+    std::vector<double> xy0(2 * size_t(N));
+    b->cs.assign(4 * size_t(k), 0.0);
+    for (int32_t m = 0; m < k; ++m) {
+        const lms_mesh_desc& d = meshes[m];
+        const int32_t vo = int32_t(b->voff[m]), eo = int32_t(eoff[m]);
+        for (int32_t v = 0; v < d.n; ++v) {
+            rp0[vo + v] = eo + d.row_ptr[v];
+            bnd0[vo + v] = d.is_boundary[v] ? 1 : 0;
+        }
+        for (int32_t e = 0; e < d.row_ptr[d.n]; ++e) ci0[eo + e] = vo + d.col_idx[e];
+        if (ordering == LMS_RDR)
+            for (int64_t i = 0; i < 3 * int64_t(d.ntri); ++i) tri0[3 * toff[m] + i] = vo + d.tri[i];
+        std::memcpy(xy0.data() + 2 * size_t(vo), d.xy, 16 * size_t(d.n));
+        double cx, cy, s;
+        bbox(d.xy, d.n, &cx, &cy, &s);
+        b->cs[4 * m] = cx;
+        b->cs[4 * m + 1] = cy;
+        b->cs[4 * m + 2] = 1.0 / s;
+        b->cs[4 * m + 3] = s;
+    }
+    rp0[N] = E;
+
+    Arena& A = b->arena;
+    Arena orig;  // original-label copies, released once the relabelled arrays exist
+    orig.al = b->arena.al;
+    orig.stream = b->stream;
+    int32_t *d_rp0 = nullptr, *d_ci0 = nullptr, *d_inv = nullptr;
+    uint8_t* d_bnd0 = nullptr;
+    auto fail_orig = [&](int rc) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        orig.release_all();
+        return fail(rc);
+    };
+    int max_items = 0;
+    for (int32_t m = 0; m < k; ++m) max_items += (meshes[m].n + 127) / 128;
+    b->items_capacity = max_items;
+    int rc = LMS_OK;
+    if ((rc = A.get(&b->d_rp, N + 1)) || (rc = A.get(&b->d_ci, std::max(1, E))) || (rc = A.get(&b->d_perm, N)) ||
+        (rc = A.get(&b->d_bits, (N + 31) / 32 + 4)) || (rc = A.get(&b->d_xy[0], N)) || (rc = A.get(&b->d_xy[1], N)) ||
+        (rc = A.get(&b->d_xy[2], N)) || (rc = A.get(&b->d_xy64, 2 * size_t(N))) || (rc = A.get(&b->d_fixed, 2 * size_t(N))) ||
+        (rc = A.get(&b->d_cs, 4 * size_t(k))) ||
+        (rc = A.get(&b->d_items, max_items)) || (rc = A.get(&b->d_item_mesh, max_items)) ||
+        (rc = ensure_queue(b, 64)) || (rc = orig.get(&d_rp0, N + 1)) || (rc = orig.get(&d_ci0, std::max(1, E))) ||
+        (rc = orig.get(&d_inv, N)) || (rc = orig.get(&d_bnd0, N)))
+        return fail_orig(rc);
+    cudaStream_t s = b->stream;
+    if (cudaMemcpyAsync(d_rp0, rp0.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d_ci0, ci0.data(), 4 * size_t(E), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d_bnd0, bnd0.data(), size_t(N), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(b->d_xy64, xy0.data(), 16 * size_t(N), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(b->d_fixed, xy0.data(), 16 * size_t(N), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(b->d_cs, b->cs.data(), 32 * size_t(k), cudaMemcpyHostToDevice, s))
+        return fail_orig(LMS_ERR_CUDA);
+
+    // RDR keys: Section 3.2 vertex qualities in FP64 on the device
+    std::vector<double> q;
+    if (ordering == LMS_RDR) {
+        std::vector<int32_t> vt_ptr, vt_idx;
+        build_incidence(N, T, tri0.data(), vt_ptr, vt_idx);
+        int32_t *d_tri = nullptr, *d_vp = nullptr, *d_vi = nullptr;
+        double *d_qt = nullptr, *d_qv = nullptr;
+        Arena tmp;
+        tmp.al = b->arena.al;
+        tmp.stream = s;
+        if ((rc = tmp.get(&d_tri, 3 * size_t(T))) || (rc = tmp.get(&d_vp, N + 1)) ||
+            (rc = tmp.get(&d_vi, 3 * size_t(T))) || (rc = tmp.get(&d_qt, T)) || (rc = tmp.get(&d_qv, N))) {
+            tmp.release_all();
+            return fail_orig(rc);
+        }
+        q.resize(N);
+        cudaError_t e = cudaMemcpyAsync(d_tri, tri0.data(), 12 * size_t(T), cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(d_vp, vt_ptr.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(d_vi, vt_idx.data(), 12 * size_t(T), cudaMemcpyHostToDevice, s);
+        if (!e) e = lms::launch_tri_quality_exact(T, d_tri, b->d_xy64, d_qt, s);
+        if (!e) e = lms::launch_vertex_quality_exact(N, d_vp, d_vi, d_qt, d_qv, s);
+        if (!e) e = cudaMemcpyAsync(q.data(), d_qv, 8 * size_t(N), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        tmp.release_all();
+        if (e) {
+            lms::set_error_detail(std::string("batch quality: ") + cudaGetErrorString(e));
+            return fail_orig(LMS_ERR_CUDA);
+        }
+    }
+    // per-mesh orderings on host threads
+    b->perm.resize(N);
+    {
+        std::atomic<int32_t> next(0);
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < nt; ++t)
+            pool.emplace_back([&]() {
+                std::vector<int32_t> p;
+                for (int32_t m; (m = next++) < k;) {
+                    const lms_mesh_desc& d = meshes[m];
+                    p.resize(d.n);
+                    const int64_t vo = b->voff[m];
+                    int r = lms::order_vertices(d.n, d.row_ptr, d.col_idx, d.is_boundary,
+                                                q.empty() ? nullptr : q.data() + vo, ordering, seed + uint64_t(m),
+                                                p.data());
+                    status[m] = r;
+                    for (int32_t i = 0; i < d.n; ++i) b->perm[vo + i] = int32_t(vo + p[i]);
+                }
+            });
+        for (auto& th : pool) th.join();
+    }
+    for (int r : status)
+        if (r != LMS_OK) return fail_orig(r);
+    // relabel on the device
+    std::vector<int32_t> inv(N), rp(N + 1);
+    for (int32_t i = 0; i < N; ++i) inv[b->perm[i]] = i;
+    rp[0] = 0;
+    for (int32_t i = 0; i < N; ++i) rp[i + 1] = rp[i] + (rp0[b->perm[i] + 1] - rp0[b->perm[i]]);
+    cudaError_t e = cudaMemcpyAsync(b->d_perm, b->perm.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_inv, inv.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(b->d_rp, rp.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
+    if (!e) e = lms::launch_gather_rows(N, b->d_perm, d_rp0, d_ci0, b->d_rp, b->d_ci, d_inv, s);
+    if (!e) e = lms::launch_boundary_bits(N, b->d_perm, d_bnd0, b->d_bits, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        lms::set_error_detail(std::string("batch relabel: ") + cudaGetErrorString(e));
+        return fail_orig(LMS_ERR_CUDA);
+    }
+    orig.release_all();
+    if ((rc = batch_build_items(b, 1024))) return fail(rc);
+    for (int i = 0; i < 2; ++i) {
+        e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy64, b->d_xy[i],
+                                      b->d_cs, s);
+        if (e) return fail(check_launch(e, "batch_load_xy"));
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LMS_ERR_CUDA);
+    *out = b;
+    return LMS_OK;
+}
+
+int lms_batch_get_config(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm) {
+    if (!b) return LMS_ERR_ARG;
+    if (block) *block = b->block;
+    if (lanes) *lanes = b->lanes;
+    if (tile) *tile = b->tile;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : lms::batch_sweep_occupancy(b->block, b->lanes);
+    return LMS_OK;
+}
+
+int lms_batch_set_config(lms_batch b, int32_t block, int32_t lanes, int32_t tile, int32_t ctas_per_sm) {
+    if (!b) return LMS_ERR_ARG;
+    if ((block != 128 && block != 256 && block != 512) || (lanes != 1 && lanes != 2 && lanes != 4) || tile < 128 ||
+        tile > 65536 || (tile % 128) != 0 || ctas_per_sm < 0)
+        return LMS_ERR_ARG;
+    b->block = block;
+    b->lanes = lanes;
+    b->tile = tile;
+    b->ctas_per_sm = ctas_per_sm;
+    b->configured = true;
+    b->graphs.clear();
+    return batch_build_items(b, tile);
+}
+
+int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm) {
+    if (!b) return LMS_ERR_ARG;
+    const char* cache = std::getenv("LMS_AUTOTUNE_CACHE");
+    const std::string key = autotune_key(b);
+    if (cache) {
+        std::ifstream f(cache);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream is(line);
+            std::string kk;
+            int bl, la, ti, cp;
+            if ((is >> kk >> bl >> la >> ti >> cp) && kk == key &&
+                lms_batch_set_config(b, bl, la, ti, cp) == LMS_OK) {
+                return lms_batch_get_config(b, block, lanes, tile, ctas_per_sm);
+            }
+        }
+    }
+    cudaStream_t s = b->stream;
+    cudaEvent_t e0, e1;
+    LMS_CUDA(cudaEventCreate(&e0));
+    LMS_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bb = 256, bl = 1, bt = 1024, bc = 0;
+    const int reps = 5;
+    LMS_TRY(ensure_queue(b, reps + 2));
+    for (int blk : {128, 256, 512})
+        for (int ln : {1, 2, 4})
+            for (int ti : {256, 512, 1024, 2048, 4096}) {
+                if (ti < blk / ln) continue;
+                b->block = blk;
+                b->lanes = ln;
+                b->ctas_per_sm = 0;
+                LMS_TRY(batch_build_items(b, ti));
+                const int grid = batch_grid(b);
+                // reads buffer cur, writes the scratch buffer: the batch's positions are untouched
+                LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * (reps + 1), s));
+                SweepArgs a = batch_args(b, b->cur, 2, reps);
+                LMS_TRY(check_launch(lms::launch_batch_sweep(a, blk, ln, grid, s), "autotune"));
+                LMS_CUDA(cudaEventRecord(e0, s));
+                for (int r = 0; r < reps; ++r) {
+                    a = batch_args(b, b->cur, 2, r);
+                    LMS_TRY(check_launch(lms::launch_batch_sweep(a, blk, ln, grid, s), "autotune"));
+                }
+                LMS_CUDA(cudaEventRecord(e1, s));
+                LMS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                LMS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bb = blk;
+                    bl = ln;
+                    bt = ti;
+                    bc = 0;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LMS_TRY(lms_batch_set_config(b, bb, bl, bt, bc));
+    if (cache) {
+        std::ofstream f(cache, std::ios::app);
+        f << key << " " << bb << " " << bl << " " << bt << " " << bc << "\n";
+    }
+    return lms_batch_get_config(b, block, lanes, tile, ctas_per_sm);
+}
+
+int lms_batch_smooth(lms_batch b, int32_t iters) {
+    if (!b || iters < 0) return LMS_ERR_ARG;
+    if (iters == 0) return LMS_OK;
+    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr));
+    LMS_TRY(ensure_queue(b, iters));
+    const int base = b->cur;
+    std::string key = std::to_string(iters) + "/" + std::to_string(base);
+    cudaGraphExec_t exec;
+    int64_t kernels = 0;
+    auto it = b->graphs.execs.find(key);
+    if (it != b->graphs.execs.end()) {
+        exec = it->second;
+        kernels = b->graphs.kernels[key];
+    } else {
+        const int grid = batch_grid(b);
+        LMS_TRY(capture(
+            b->cap,
+            [&](cudaStream_t cs) -> int {
+                LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * iters, cs));
+                for (int32_t i = 0; i < iters; ++i) {
+                    const int src = (base + i) & 1;
+                    SweepArgs a = batch_args(b, src, src ^ 1, i);
+                    LMS_TRY(check_launch(lms::launch_batch_sweep(a, b->block, b->lanes, grid, cs), "batch_sweep"));
+                }
+                return LMS_OK;
+            },
+            &exec, &kernels));
+        b->graphs.execs[key] = exec;
+        b->graphs.kernels[key] = kernels;
+    }
+    LMS_CUDA(cudaGraphLaunch(exec, b->stream));
+    b->last_launches = kernels;
+    b->cur = (base + iters) & 1;
+    return LMS_OK;
+}
+
+int lms_batch_get_all_coords(lms_batch b, double* xy) {
+    if (!b || !xy) return LMS_ERR_ARG;
+    cudaStream_t s = b->stream;
+    LMS_TRY(check_launch(lms::launch_batch_store_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy[b->cur],
+                                                    b->d_xy64, b->d_cs, b->d_bits, b->d_fixed, s),
+                         "batch_store_xy"));
+    LMS_CUDA(cudaMemcpyAsync(xy, b->d_xy64, 16 * size_t(b->n_total), cudaMemcpyDeviceToHost, s));
+    LMS_CUDA(cudaStreamSynchronize(s));
+    return LMS_OK;
+}
+
+int lms_batch_get_coords(lms_batch b, int32_t mesh, double* xy) {
+    if (!b || !xy || mesh < 0 || mesh >= b->k) return LMS_ERR_ARG;
+    cudaStream_t s = b->stream;
+    LMS_TRY(check_launch(lms::launch_batch_store_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy[b->cur],
+                                                    b->d_xy64, b->d_cs, b->d_bits, b->d_fixed, s),
+                         "batch_store_xy"));
+    const int64_t v0 = b->voff[mesh], nv = b->voff[mesh + 1] - v0;
+    LMS_CUDA(cudaMemcpyAsync(xy, b->d_xy64 + 2 * v0, 16 * size_t(nv), cudaMemcpyDeviceToHost, s));
+    LMS_CUDA(cudaStreamSynchronize(s));
+    return LMS_OK;
+}
+
+int lms_batch_set_all_coords(lms_batch b, const double* xy) {
+    if (!b || !xy) return LMS_ERR_ARG;
+    if (!all_finite(xy, 2 * b->n_total)) return LMS_ERR_ARG;
+    cudaStream_t s = b->stream;
+    LMS_CUDA(cudaMemcpyAsync(b->d_xy64, xy, 16 * size_t(b->n_total), cudaMemcpyHostToDevice, s));
+    LMS_CUDA(cudaMemcpyAsync(b->d_fixed, b->d_xy64, 16 * size_t(b->n_total), cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < 2; ++i)
+        LMS_TRY(check_launch(lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy64,
+                                                       b->d_xy[i], b->d_cs, s),
+                             "batch_load_xy"));
+    b->cur = 0;
+    return LMS_OK;
+}
+
+int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles) {
+    if (!b) return LMS_ERR_ARG;
+    if (n_total) *n_total = b->n_total;
+    if (n_interior) *n_interior = b->n_int;
+    if (nnz_total) *nnz_total = b->nnz_total;
+    if (n_tiles) *n_tiles = b->n_items;
+    return LMS_OK;
+}
+
+int lms_batch_last_launches(lms_batch b, int64_t* launches) {
+    if (!b || !launches) return LMS_ERR_ARG;
+    *launches = b->last_launches;
+    return LMS_OK;
+}
+
+int lms_batch_get_permutation(lms_batch b, int32_t mesh, int32_t* new_to_old) {
+    if (!b || !new_to_old || mesh < 0 || mesh >= b->k) return LMS_ERR_ARG;
+    const int64_t v0 = b->voff[mesh], nv = b->voff[mesh + 1] - v0;
+    for (int64_t i = 0; i < nv; ++i) new_to_old[i] = int32_t(b->perm[v0 + i] - v0);
+    return LMS_OK;
+}
+
+void lms_batch_destroy(lms_batch b) { delete b; }
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// lms_host.cpp - host-side logic of liblms: mesh validation, the four vertex
+// orderings and the first-fit colouring.  Pure C++, no device work; built with
+// -ffp-contract=off (the only floating-point work here is comparing keys).
+//
+// Orderings follow Aupy, Park & Raghavan, "Locality-Aware Laplacian Mesh
+// Smoothing": ORI and BFS as compared in Section 5.2.1, a random ordering as in
+// Fig. 1a, and the Reuse Distance Reducing ordering of Algorithm 2
+// (Section 4.2).  Readings where the paper is silent:
+//   RDR  - keys are (vertex quality, id) ascending; the walk's neighbour lists
+//          include boundary vertices; l[0] is the worst member of l; vertices no
+//          walk reaches are appended in ascending id (Theorem 1 then holds for
+//          every vertex, not only the interior ones its proof covers);
+//   BFS  - from vertex 0, neighbours in ascending id, restart at the smallest
+//          unvisited id;
+//   RANDOM - Fisher-Yates, i = n-1 .. 1, j = splitmix64() mod (i+1).
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <vector>
+
+#include "lms_internal.h"
+
+namespace lms {
+
+namespace {
+thread_local std::string g_detail;
+
+inline int32_t row_len(const int32_t* row_ptr, int32_t v) { return row_ptr[v + 1] - row_ptr[v]; }
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014): state advances by the golden gamma, output is
+// the state passed through a variant of the MurmurHash3 finaliser.
+struct SplitMix64 {
+    uint64_t state;
+    uint64_t next() {
+        state += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+};
+
+// Strict total order of Algorithm 2's sort keys.
+struct KeyLess {
+    const double* q;
+    bool operator()(int32_t a, int32_t b) const { return q[a] < q[b] || (q[a] == q[b] && a < b); }
+};
+
+void order_random(int32_t n, uint64_t seed, int32_t* out) {
+    for (int32_t i = 0; i < n; ++i) out[i] = i;
+    SplitMix64 g{seed};
+    for (int32_t i = n - 1; i > 0; --i) {
+        uint64_t j = g.next() % static_cast<uint64_t>(i + 1);
+        std::swap(out[i], out[j]);
+    }
+}
+
+void order_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* out) {
+    std::vector<uint8_t> visited(n, 0);
+    std::vector<int32_t> nb;
+    int32_t written = 0, read = 0, next_root = 0;
+    while (written < n) {
+        while (visited[next_root]) ++next_root;
+        visited[next_root] = 1;
+        out[written++] = next_root;
+        while (read < written) {
+            int32_t v = out[read++];
+            nb.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
+            std::sort(nb.begin(), nb.end());
+            for (int32_t u : nb)
+                if (!visited[u]) {
+                    visited[u] = 1;
+                    out[written++] = u;
+                }
+        }
+    }
+}
+
+// Algorithm 2.  `done` = processed (the walk has expanded the vertex), `placed` = sorted (it has a
+// position in the new order).
+void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+               const double* q, int32_t* out) {
+    KeyLess less{q};
+    std::vector<int32_t> seeds;
+    seeds.reserve(n);
+    for (int32_t v = 0; v < n; ++v)
+        if (!is_boundary[v]) seeds.push_back(v);
+    std::sort(seeds.begin(), seeds.end(), less);
+
+    std::vector<uint8_t> done(n, 0), placed(n, 0);
+    std::vector<int32_t> l;
+    int32_t pos = 0;
+    auto place = [&](int32_t v) {
+        if (!placed[v]) {
+            placed[v] = 1;
+            out[pos++] = v;
+        }
+    };
+    // l <- unprocessed neighbours of v by increasing key (rows are short: insertion sort)
+    auto gather = [&](int32_t v) {
+        l.clear();
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t u = col_idx[e];
+            if (done[u]) continue;
+            l.push_back(u);
+            for (size_t k = l.size() - 1; k > 0 && less(l[k], l[k - 1]); --k) std::swap(l[k], l[k - 1]);
+        }
+    };
+    for (int32_t s : seeds) {
+        if (done[s]) continue;
+        place(s);
+        done[s] = 1;
+        gather(s);
+        while (!l.empty()) {
+            for (int32_t u : l) place(u);
+            int32_t w = l.front();
+            done[w] = 1;
+            gather(w);
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) place(v);  // vertices no walk reached, ascending id
+}
+}  // namespace
+
+void set_error_detail(const std::string& s) { g_detail = s; }
+const std::string& error_detail() { return g_detail; }
+
+int validate_mesh(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                  int32_t ntri, const int32_t* tri) {
+    if (n <= 0 || !row_ptr || !is_boundary || ntri < 0 || (ntri > 0 && !tri)) return LMS_ERR_ARG;
+    if (row_ptr[0] != 0) return LMS_ERR_CSR;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return LMS_ERR_CSR;
+    const int32_t nnz = row_ptr[n];
+    if (nnz > 0 && !col_idx) return LMS_ERR_ARG;
+    for (int32_t e = 0; e < nnz; ++e)
+        if (col_idx[e] < 0 || col_idx[e] >= n) return LMS_ERR_CSR;
+    // sorted copy of every row: self-loops, duplicates, and symmetry by binary search
+    std::vector<int32_t> sorted(col_idx, col_idx + nnz);
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t* r = sorted.data() + row_ptr[v];
+        std::sort(r, r + row_len(row_ptr, v));
+        for (int32_t k = 0; k < row_len(row_ptr, v); ++k) {
+            if (r[k] == v) return LMS_ERR_CSR;
+            if (k > 0 && r[k] == r[k - 1]) return LMS_ERR_CSR;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t u = sorted[e];
+            const int32_t* b = sorted.data() + row_ptr[u];
+            if (!std::binary_search(b, b + row_len(row_ptr, u), v)) return LMS_ERR_CSR;
+        }
+    for (int32_t v = 0; v < n; ++v)
+        if (!is_boundary[v] && row_len(row_ptr, v) == 0) return LMS_ERR_ISOLATED;
+    for (int64_t t = 0; t < ntri; ++t) {
+        int32_t a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n) return LMS_ERR_ARG;
+        if (a == b || b == c || a == c) return LMS_ERR_ARG;
+    }
+    return LMS_OK;
+}
+
+int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const double* q_v, int ordering, uint64_t seed, int32_t* new_to_old) {
+    if (n <= 0 || !row_ptr || !new_to_old) return LMS_ERR_ARG;
+    switch (ordering) {
+        case LMS_ORI:
+            for (int32_t i = 0; i < n; ++i) new_to_old[i] = i;
+            return LMS_OK;
+        case LMS_RANDOM:
+            order_random(n, seed, new_to_old);
+            return LMS_OK;
+        case LMS_BFS:
+            if (!col_idx && row_ptr[n] > 0) return LMS_ERR_ARG;
+            order_bfs(n, row_ptr, col_idx, new_to_old);
+            return LMS_OK;
+        case LMS_RDR:
+            if (!q_v || !is_boundary || (!col_idx && row_ptr[n] > 0)) return LMS_ERR_ARG;
+            order_rdr(n, row_ptr, col_idx, is_boundary, q_v, new_to_old);
+            return LMS_OK;
+        default:
+            return LMS_ERR_ARG;
+    }
+}
+
+int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours) {
+    if (n <= 0 || !row_ptr || !is_boundary || !new_to_old || !colour || !ncolours) return LMS_ERR_ARG;
+    std::fill(colour, colour + n, -1);
+    std::vector<uint8_t> taken;
+    int32_t count = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t v = new_to_old[k];
+        if (v < 0 || v >= n) return LMS_ERR_ARG;
+        if (is_boundary[v]) continue;
+        uint64_t mask = 0;  // colours 0..63 of coloured neighbours; larger ones tracked in `taken`
+        bool wide = false;
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t c = colour[col_idx[e]];
+            if (c < 0) continue;
+            if (c < 64) {
+                mask |= 1ULL << c;
+            } else {
+                if (!wide) {
+                    taken.assign(row_len(row_ptr, v) + 1, 0);
+                    wide = true;
+                }
+                if (c - 64 < static_cast<int32_t>(taken.size())) taken[c - 64] = 1;
+            }
+        }
+        int32_t c;
+        if (~mask != 0) {
+            c = __builtin_ctzll(~mask);
+        } else {
+            c = 64;
+            while (wide && c - 64 < static_cast<int32_t>(taken.size()) && taken[c - 64]) ++c;
+        }
+        colour[v] = c;
+        count = std::max(count, c + 1);
+    }
+    *ncolours = count;
+    return LMS_OK;
+}
+
+}  // namespace lms
+
+extern "C" {
+
+const char* lms_error_string(int status) {
+    switch (status) {
+        case LMS_OK: return "ok";
+        case LMS_ERR_ARG: return "invalid argument (NULL pointer, bad enum, size or index out of range)";
+        case LMS_ERR_CSR: return "invalid CSR adjacency (offsets, range, self-loop, duplicate or asymmetry)";
+        case LMS_ERR_ISOLATED: return "interior vertex without neighbours";
+        case LMS_ERR_NO_TRIANGLES: return "operation needs triangles, none were given";
+        case LMS_ERR_CUDA: return "CUDA runtime error";
+        case LMS_ERR_OOM: return "out of memory";
+        case LMS_ERR_TIMEOUT: return "bounded device-side wait expired";
+        case LMS_ERR_STATE: return "call not valid in the current state";
+        default: return "unknown status";
+    }
+}
+
+int lms_validate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                 int32_t ntri, const int32_t* tri) {
+    return lms::validate_mesh(n, row_ptr, col_idx, is_boundary, ntri, tri);
+}
+
+int lms_order_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const double* q_v, int ordering, uint64_t seed, int32_t* new_to_old) {
+    return lms::order_vertices(n, row_ptr, col_idx, is_boundary, q_v, ordering, seed, new_to_old);
+}
+
+int lms_color_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const int32_t* new_to_old, int32_t* colour, int32_t* ncolours) {
+    return lms::colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour, ncolours);
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// lms_internal.h - declarations shared by the host code (lms_host.cpp), the
+// C-ABI layer (lms_capi.cpp) and the CUDA kernels (lms_kernels.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lms.h"
+
+namespace lms {
+
+// ----------------------------------------------------------------- host side
+
+// Structural checks of a CSR mesh (see lms_validate in lms.h).
+int validate_mesh(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                  int32_t ntri, const int32_t* tri);
+
+// Orderings (Section 4.2 / Algorithm 2, Section 5.2.1).  new_to_old[k] = original id at position k.
+int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const double* q_v, int ordering, uint64_t seed, int32_t* new_to_old);
+
+// First-fit colouring of interior vertices in storage order; colour indexed by original id.
+int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours);
+
+// Set the message reported with LMS_ERR_CUDA and friends (thread-local).
+void set_error_detail(const std::string& s);
+const std::string& error_detail();
+
+// ------------------------------------------------------------- device side
+
+constexpr int kMaxRecipDeg = 64;  // reciprocal table size for the exact FP64 division
+
+// State shared by the sweep, quality and stop-check kernels of one handle.
+struct DevState {
+    double q_prev;                 // Q of the previous sweep
+    double q_cur;                  // Q of the latest sweep (or of lms_quality)
+    double q_first;                // Q_0
+    unsigned long long disp2[2];   // max squared displacement, by sweep parity (bits of a double >= 0)
+    int32_t stop;                  // set by the stop check once the rule fires
+    int32_t k;                     // sweeps completed under the stopping rule
+    int32_t iters_at_stop;         // sweep index at which the rule fired
+    int32_t err;                   // nonzero: a device-side check failed
+};
+
+struct SweepArgs {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const uint32_t* bnd_bits;      // bit v set = boundary (NULL: every vertex in range is interior)
+    const void* src;               // double2 / float2 positions read
+    void* dst;                     // positions written (== src for the in-place coloured sweep)
+    int32_t v_begin, v_end;        // vertex range of a static launch
+    const int2* items;             // work-queue tiles (batched)
+    int32_t n_items;
+    int32_t* queue;                // work-queue counter for this sweep
+    const DevState* state;         // stop flag (NULL: never stop)
+    unsigned long long* disp2;     // max squared displacement accumulator (NULL: off)
+    const double* recip;           // [kMaxRecipDeg+1] RN(1/d) for the FP64 exact division
+};
+
+// Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
+cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, cudaStream_t stream);
+int batch_sweep_occupancy(int block, int lanes);  // resident CTAs per SM (0 on error)
+
+cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
+                                     cudaStream_t stream);
+cudaError_t launch_vertex_quality_exact(int32_t n, const int32_t* vt_ptr, const int32_t* vt_idx,
+                                        const double* q_t, double* q_v, cudaStream_t stream);
+// Per-sweep quality: partial sums of w_t * q_t over a fixed grid of nblocks, then a fixed-order finish.
+constexpr int kQualityBlocks = 1024;
+cudaError_t launch_quality_partials(int precision, int32_t ntri, const int32_t* tri, const void* xy,
+                                    const double* w, double* partials, const DevState* state,
+                                    cudaStream_t stream);
+// Q = (sum of partials) / n.  mode 0: store into q_cur; mode 1: Q_0 (q_first = q_prev = q_cur = Q).
+cudaError_t launch_quality_finish(const double* partials, double n, DevState* state, int mode, cudaStream_t stream);
+// Stop check after a sweep (Section 5.1 rule + iteration cap); skipped once the rule has fired.
+cudaError_t launch_stop_check(const double* partials, double n, DevState* state, double tol, double goal,
+                              int32_t max_iters, cudaStream_t stream);
+
+cudaError_t launch_gather_rows(int32_t n, const int32_t* new_to_old, const int32_t* rp_src, const int32_t* ci_src,
+                               const int32_t* rp_dst, int32_t* ci_dst, const int32_t* map, cudaStream_t stream);
+cudaError_t launch_map_ids(int64_t count, const int32_t* map, const int32_t* src, int32_t* dst,
+                           cudaStream_t stream);
+cudaError_t launch_boundary_bits(int32_t n, const int32_t* new_to_old, const uint8_t* bnd_orig, uint32_t* bits,
+                                 cudaStream_t stream);
+// dst[k] = src[perm[k]] for 16-byte (double2) or 8-byte (float2) elements
+cudaError_t launch_gather_xy(int precision, int32_t n, const int32_t* perm, const void* src, void* dst,
+                             cudaStream_t stream);
+// original-order FP64 input -> storage-order positions: dst[k] = f(src[new_to_old[k]])
+// precision FP32: normalised with (cx, cy, inv_s); item_mesh/item ranges give per-mesh constants when given
+cudaError_t launch_load_xy(int precision, int32_t n, const int32_t* new_to_old, const double* src_orig, void* dst,
+                           double cx, double cy, double inv_s, cudaStream_t stream);
+// storage-order positions -> original-order FP64: dst[new_to_old[k]] = g(src[k]); FP32 boundary vertices
+// are taken from fixed_xy (original order) when it is given
+cudaError_t launch_store_xy(int precision, int32_t n, const int32_t* new_to_old, const void* src, double* dst_orig,
+                            double cx, double cy, double s, const uint8_t* bnd_orig, const double* fixed_xy,
+                            cudaStream_t stream);
+// batched: per-tile mesh constants (tile t covers items[t], belongs to mesh item_mesh[t])
+cudaError_t launch_batch_load_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
+                                 const int32_t* new_to_old, const double* src_orig, float2* dst,
+                                 const double* mesh_cs, cudaStream_t stream);
+cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
+                                  const int32_t* new_to_old, const float2* src, double* dst_orig,
+                                  const double* mesh_cs, const uint32_t* bnd_bits, const double* fixed_xy,
+                                  cudaStream_t stream);
+
+// Diagnostic: q[i] = s[i] / d[i] by the table-driven exact division used in the FP64 sweep.
+cudaError_t launch_div_selftest(int32_t count, const double* s, const int32_t* d, const double* recip, double* q,
+                                cudaStream_t stream);
+
+}  // namespace lms

@@ -1,0 +1,585 @@
+// lms_kernels.cu - sm_103a kernels of liblms.
+//
+// The hot loop is Eq. 1 of Aupy, Park & Raghavan, "Locality-Aware Laplacian
+// Mesh Smoothing": every interior vertex moves to the mean of its mesh
+// neighbours.  It is a sparse CSR gather (no dense contraction, so no tensor
+// cores): per interior vertex the sweep streams its row offset and its
+// neighbour ids, gathers the neighbours' positions (mostly L1/L2 hits when the
+// ordering keeps neighbours close in memory - the point of BFS and RDR) and
+// writes one position.
+//
+// Arithmetic contracts (all explicit _rn intrinsics, so no FMA contraction
+// changes a result):
+//   FP64  sums run left to right over the stored row starting from 0.0, and
+//         the mean is the correctly rounded quotient; results equal the
+//         sequential FP64 evaluation of Eq. 1 bit for bit.  The quotient by the
+//         neighbour count d uses y = RN(1/d) from a table, q = RN(s*y) and one
+//         correction RN(q + RN(s - d*q)*y) (Markstein's division refinement,
+//         IBM J. Res. Dev. 34(1), 1990); it is checked against IEEE division by
+//         the division self-test.  GB300 runs FP64 at ~1/64 of the FP32 rate,
+//         and this is ~3 FP64 operations instead of a full division.
+//   FP32  coordinates are relative to the bounding-box centre and scaled to
+//         unit size; neighbour sums are Kahan-compensated; quality sums are
+//         reduced in FP64.
+#include <cfloat>
+#include <cstdint>
+
+#include "lms_internal.h"
+
+namespace lms {
+
+namespace {
+
+__device__ __forceinline__ bool boundary_bit(const uint32_t* __restrict__ bits, int32_t v) {
+    return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// s / d for a positive integer d, correctly rounded (see the file header).
+__device__ __forceinline__ double div_by_count(double s, int32_t d, const double* recip) {
+    if (d <= kMaxRecipDeg) {
+        const double y = recip[d];
+        const double q = __dmul_rn(s, y);
+        const double r = __fma_rn(-q, static_cast<double>(d), s);
+        return __fma_rn(r, y, q);
+    }
+    return __ddiv_rn(s, static_cast<double>(d));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void record_disp(unsigned long long* disp2, double d2) {
+    // non-negative doubles order like their bit patterns
+    unsigned long long m = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(d2)));
+    if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(disp2, m);
+}
+
+// Eq. 1 for one vertex, FP64.  Returns the squared displacement when asked.
+template <bool IN_PLACE>
+__device__ __forceinline__ double smooth_vertex_f64(const SweepArgs& a, int32_t v, const double* recip,
+                                                    bool want_disp) {
+    const double2* src = static_cast<const double2*>(a.src);
+    double2* dst = static_cast<double2*>(a.dst);
+    const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+    double sx = 0.0, sy = 0.0;
+    for (int32_t e = e0; e < e1; ++e) {
+        const int32_t u = __ldg(a.col_idx + e);
+        const double2 p = IN_PLACE ? src[u] : __ldg(src + u);
+        sx = __dadd_rn(sx, p.x);
+        sy = __dadd_rn(sy, p.y);
+    }
+    double2 r;
+    r.x = div_by_count(sx, e1 - e0, recip);
+    r.y = div_by_count(sy, e1 - e0, recip);
+    double d2 = 0.0;
+    if (want_disp) {
+        const double2 o = src[v];
+        const double dx = __dsub_rn(r.x, o.x), dy = __dsub_rn(r.y, o.y);
+        d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    }
+    dst[v] = r;
+    return d2;
+}
+
+// Eq. 1 for one vertex, FP32 with compensated sums.
+template <bool IN_PLACE>
+__device__ __forceinline__ double smooth_vertex_f32(const SweepArgs& a, int32_t v, bool want_disp) {
+    const float2* src = static_cast<const float2*>(a.src);
+    float2* dst = static_cast<float2*>(a.dst);
+    const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    for (int32_t e = e0; e < e1; ++e) {
+        const int32_t u = __ldg(a.col_idx + e);
+        const float2 p = IN_PLACE ? src[u] : __ldg(src + u);
+        kahan_add(sx, cx, p.x);
+        kahan_add(sy, cy, p.y);
+    }
+    const float d = static_cast<float>(e1 - e0);
+    float2 r;
+    r.x = __fdiv_rn(__fsub_rn(sx, cx), d);
+    r.y = __fdiv_rn(__fsub_rn(sy, cy), d);
+    double d2 = 0.0;
+    if (want_disp) {
+        const float2 o = src[v];
+        const double dx = static_cast<double>(__fsub_rn(r.x, o.x)), dy = static_cast<double>(__fsub_rn(r.y, o.y));
+        d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    }
+    dst[v] = r;
+    return d2;
+}
+
+// One thread per vertex over [v_begin, v_end).  Jacobi: src != dst, boundary vertices skipped
+// (both ping-pong buffers hold them).  Coloured GS: src == dst, every vertex of the range is
+// interior and of one colour, so no two threads touch neighbouring vertices.
+template <bool FP64, bool IN_PLACE>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+    if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
+    __shared__ double s_recip[kMaxRecipDeg + 1];
+    if (FP64) {
+        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
+        __syncthreads();
+    }
+    const int32_t v = a.v_begin + static_cast<int32_t>(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool want = a.disp2 != nullptr;
+    double d2 = 0.0;
+    if (v < a.v_end && (a.bnd_bits == nullptr || !boundary_bit(a.bnd_bits, v))) {
+        if (FP64)
+            d2 = smooth_vertex_f64<IN_PLACE>(a, v, s_recip, want);
+        else
+            d2 = smooth_vertex_f32<IN_PLACE>(a, v, want);
+    }
+    if (want) record_disp(a.disp2, d2);
+}
+
+// Batched FP32 Jacobi: a persistent grid pulls vertex tiles from a device counter.  LANES lanes
+// share one vertex: each Kahan-sums every LANES-th neighbour, then the partial sums are merged
+// with shuffles (compensations folded in first).
+template <int LANES>
+__global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
+    __shared__ int32_t s_item[2];
+    const float2* __restrict__ src = static_cast<const float2*>(a.src);
+    float2* __restrict__ dst = static_cast<float2*>(a.dst);
+    const int group = threadIdx.x / LANES, sub = threadIdx.x % LANES;
+    const int groups = blockDim.x / LANES;
+    int buf = 0;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    for (;;) {
+        const int32_t item = s_item[buf];
+        if (item >= a.n_items) break;
+        if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
+        const int2 r = __ldg(a.items + item);
+        for (int32_t base = r.x; base < r.y; base += groups) {
+            const int32_t v = base + group;
+            bool active = v < r.y && !boundary_bit(a.bnd_bits, v);
+            int32_t e0 = 0, e1 = 0;
+            if (active) {
+                e0 = __ldg(a.row_ptr + v);
+                e1 = __ldg(a.row_ptr + v + 1);
+            }
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int32_t e = e0 + sub; e < e1; e += LANES) {
+                const float2 p = __ldg(src + __ldg(a.col_idx + e));
+                kahan_add(sx, cx, p.x);
+                kahan_add(sy, cy, p.y);
+            }
+            float tx = __fsub_rn(sx, cx), ty = __fsub_rn(sy, cy);
+            if (LANES > 1) {
+                float kx = 0.f, ky = 0.f;
+#pragma unroll
+                for (int o = 1; o < LANES; o <<= 1) {
+                    const float ox = __shfl_xor_sync(0xffffffffu, tx, o);
+                    const float oy = __shfl_xor_sync(0xffffffffu, ty, o);
+                    const float okx = __shfl_xor_sync(0xffffffffu, kx, o);
+                    const float oky = __shfl_xor_sync(0xffffffffu, ky, o);
+                    // two-sum of the partials, carrying the rounding error
+                    const float x = __fadd_rn(tx, ox), bx = __fsub_rn(x, tx);
+                    kx = __fadd_rn(__fadd_rn(kx, okx), __fadd_rn(__fsub_rn(tx, __fsub_rn(x, bx)), __fsub_rn(ox, bx)));
+                    tx = x;
+                    const float y = __fadd_rn(ty, oy), by = __fsub_rn(y, ty);
+                    ky = __fadd_rn(__fadd_rn(ky, oky), __fadd_rn(__fsub_rn(ty, __fsub_rn(y, by)), __fsub_rn(oy, by)));
+                    ty = y;
+                }
+                tx = __fadd_rn(tx, kx);
+                ty = __fadd_rn(ty, ky);
+            }
+            if (active && sub == 0) {
+                const float d = static_cast<float>(e1 - e0);
+                dst[v] = make_float2(__fdiv_rn(tx, d), __fdiv_rn(ty, d));
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+// Section 3.2 edge-length ratio, written exactly as the definition: three correctly rounded
+// lengths, shortest over longest.
+__device__ __forceinline__ double edge_len_exact(double2 p, double2 q) {
+    const double dx = __dsub_rn(q.x, p.x), dy = __dsub_rn(q.y, p.y);
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+}
+
+__global__ void k_tri_quality_exact(int32_t ntri, const int32_t* __restrict__ tri, const double2* __restrict__ xy,
+                                    double* __restrict__ q_t) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntri) return;
+    const double2 a = xy[tri[3 * t]], b = xy[tri[3 * t + 1]], c = xy[tri[3 * t + 2]];
+    const double l0 = edge_len_exact(a, b), l1 = edge_len_exact(b, c), l2 = edge_len_exact(c, a);
+    double lo = l0, hi = l0;
+    lo = l1 < lo ? l1 : lo;
+    hi = l1 > hi ? l1 : hi;
+    lo = l2 < lo ? l2 : lo;
+    hi = l2 > hi ? l2 : hi;
+    q_t[t] = hi == 0.0 ? 0.0 : __ddiv_rn(lo, hi);
+}
+
+// Mean over a vertex's triangles, in ascending triangle id (the incidence rows are ascending).
+__global__ void k_vertex_quality_exact(int32_t n, const int32_t* __restrict__ vt_ptr,
+                                       const int32_t* __restrict__ vt_idx, const double* __restrict__ q_t,
+                                       double* __restrict__ q_v) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t e0 = vt_ptr[v], e1 = vt_ptr[v + 1];
+    double s = 0.0;
+    for (int32_t e = e0; e < e1; ++e) s = __dadd_rn(s, q_t[vt_idx[e]]);
+    q_v[v] = e1 > e0 ? __ddiv_rn(s, static_cast<double>(e1 - e0)) : 0.0;
+}
+
+// Per-sweep quality.  Q = (1/n) sum_v (1/n_t(v)) sum_{t in v} q_t = (1/n) sum_t w_t q_t with
+// w_t = sum over t's corners of 1/n_t(corner): one pass over the triangles.  q_t uses the same
+// ratio written as sqrt(min l^2 / max l^2) (one root instead of three).
+__device__ __forceinline__ double tri_quality_fast(double2 a, double2 b, double2 c) {
+    const double e0 = (b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y);
+    const double e1 = (c.x - b.x) * (c.x - b.x) + (c.y - b.y) * (c.y - b.y);
+    const double e2 = (a.x - c.x) * (a.x - c.x) + (a.y - c.y) * (a.y - c.y);
+    const double lo = fmin(e0, fmin(e1, e2)), hi = fmax(e0, fmax(e1, e2));
+    return hi > 0.0 ? sqrt(lo / hi) : 0.0;
+}
+
+__device__ __forceinline__ double tri_quality_fast(float2 a, float2 b, float2 c) {
+    const float e0 = (b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y);
+    const float e1 = (c.x - b.x) * (c.x - b.x) + (c.y - b.y) * (c.y - b.y);
+    const float e2 = (a.x - c.x) * (a.x - c.x) + (a.y - c.y) * (a.y - c.y);
+    const float lo = fminf(e0, fminf(e1, e2)), hi = fmaxf(e0, fmaxf(e1, e2));
+    return hi > 0.f ? static_cast<double>(sqrtf(lo / hi)) : 0.0;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += smem[w];
+    return s;  // valid in thread 0
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_quality_partials(int32_t ntri, const int32_t* __restrict__ tri,
+                                                          const V* __restrict__ xy, const double* __restrict__ w,
+                                                          double* __restrict__ partials, const DevState* state) {
+    __shared__ double smem[32];
+    if (state != nullptr && *reinterpret_cast<const volatile int32_t*>(&state->stop)) return;
+    double acc = 0.0;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += gridDim.x * blockDim.x) {
+        const V a = __ldg(xy + __ldg(tri + 3 * t)), b = __ldg(xy + __ldg(tri + 3 * t + 1)),
+                c = __ldg(xy + __ldg(tri + 3 * t + 2));
+        acc += __ldg(w + t) * tri_quality_fast(a, b, c);
+    }
+    const double s = block_sum(acc, smem);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kQualityBlocks) k_quality_finish(const double* __restrict__ partials,
+                                                                   double n, DevState* st, int mode) {
+    __shared__ double smem[32];
+    const double s = block_sum(partials[threadIdx.x], smem);
+    if (threadIdx.x != 0) return;
+    const double Q = s / n;
+    if (mode == 0) {
+        st->q_cur = Q;
+    } else if (mode == 1) {
+        st->q_first = Q;
+        st->q_prev = Q;
+        st->q_cur = Q;
+    }
+}
+
+// Stop check after sweep k (Section 5.1): the rule fires when Q_k - Q_{k-1} < tol (or Q_k >= goal);
+// the cap fires at max_iters.  Also clears the displacement slot of sweep k+1.
+__global__ void k_stop_check(const double* __restrict__ partials, double n, DevState* st, double tol, double goal,
+                             int32_t max_iters) {
+    __shared__ double smem[32];
+    if (*reinterpret_cast<volatile int32_t*>(&st->stop)) return;
+    const double s = block_sum(partials[threadIdx.x], smem);
+    if (threadIdx.x != 0) return;
+    const double Q = s / n;
+    const int32_t k = st->k + 1;
+    st->k = k;
+    if (Q >= goal || Q - st->q_prev < tol || k >= max_iters) {
+        st->stop = 1;
+        st->iters_at_stop = k;
+    }
+    st->q_prev = Q;
+    st->q_cur = Q;
+    st->disp2[(k + 1) & 1] = 0ull;
+}
+
+__global__ void k_gather_rows(int32_t n, const int32_t* __restrict__ new_to_old, const int32_t* __restrict__ rp_src,
+                              const int32_t* __restrict__ ci_src, const int32_t* __restrict__ rp_dst,
+                              int32_t* __restrict__ ci_dst, const int32_t* __restrict__ map) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t v = new_to_old[k];
+    const int32_t s0 = rp_src[v], len = rp_src[v + 1] - s0, d0 = rp_dst[k];
+    for (int32_t e = 0; e < len; ++e) {
+        const int32_t u = ci_src[s0 + e];
+        ci_dst[d0 + e] = map ? map[u] : u;
+    }
+}
+
+__global__ void k_map_ids(int64_t count, const int32_t* __restrict__ map, const int32_t* __restrict__ src,
+                          int32_t* __restrict__ dst) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = map[src[i]];
+}
+
+__global__ void k_boundary_bits(int32_t n, const int32_t* __restrict__ new_to_old,
+                                const uint8_t* __restrict__ bnd_orig, uint32_t* __restrict__ bits) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim is a multiple of 32
+    const bool b = k < n && bnd_orig[new_to_old[k]] != 0;
+    const uint32_t word = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && k < n) bits[k >> 5] = word;
+}
+
+template <typename V>
+__global__ void k_gather_xy(int32_t n, const int32_t* __restrict__ perm, const V* __restrict__ src,
+                            V* __restrict__ dst) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[perm[k]];
+}
+
+__global__ void k_load_xy_f64(int32_t n, const int32_t* __restrict__ new_to_old, const double2* __restrict__ src,
+                              double2* __restrict__ dst) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[new_to_old[k]];
+}
+
+__device__ __forceinline__ float2 normalise(double2 p, double cx, double cy, double inv_s) {
+    return make_float2(__double2float_rn(__dmul_rn(__dsub_rn(p.x, cx), inv_s)),
+                       __double2float_rn(__dmul_rn(__dsub_rn(p.y, cy), inv_s)));
+}
+
+__device__ __forceinline__ double2 denormalise(float2 p, double cx, double cy, double s) {
+    return make_double2(__dadd_rn(cx, __dmul_rn(s, static_cast<double>(p.x))),
+                        __dadd_rn(cy, __dmul_rn(s, static_cast<double>(p.y))));
+}
+
+__global__ void k_load_xy_f32(int32_t n, const int32_t* __restrict__ new_to_old, const double2* __restrict__ src,
+                              float2* __restrict__ dst, double cx, double cy, double inv_s) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = normalise(src[new_to_old[k]], cx, cy, inv_s);
+}
+
+__global__ void k_store_xy_f64(int32_t n, const int32_t* __restrict__ new_to_old, const double2* __restrict__ src,
+                               double2* __restrict__ dst) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[new_to_old[k]] = src[k];
+}
+
+// Boundary vertices never move: they are returned as the FP64 values last stored (fixed_xy, original
+// order), not as their FP32 copies mapped back.
+__global__ void k_store_xy_f32(int32_t n, const int32_t* __restrict__ new_to_old, const float2* __restrict__ src,
+                               double2* __restrict__ dst, double cx, double cy, double s,
+                               const uint8_t* __restrict__ bnd_orig, const double2* __restrict__ fixed_xy) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t o = new_to_old[k];
+    dst[o] = (fixed_xy != nullptr && bnd_orig[o]) ? fixed_xy[o] : denormalise(src[k], cx, cy, s);
+}
+
+// one block per tile; mesh_cs[4m..4m+3] = (cx, cy, inv_s, s)
+__global__ void k_batch_load_xy(const int2* __restrict__ items, const int32_t* __restrict__ item_mesh,
+                                const int32_t* __restrict__ new_to_old, const double2* __restrict__ src,
+                                float2* __restrict__ dst, const double* __restrict__ mesh_cs) {
+    const int2 r = items[blockIdx.x];
+    const double* cs = mesh_cs + 4 * item_mesh[blockIdx.x];
+    for (int32_t k = r.x + threadIdx.x; k < r.y; k += blockDim.x) dst[k] = normalise(src[new_to_old[k]], cs[0], cs[1], cs[2]);
+}
+
+__global__ void k_batch_store_xy(const int2* __restrict__ items, const int32_t* __restrict__ item_mesh,
+                                 const int32_t* __restrict__ new_to_old, const float2* __restrict__ src,
+                                 double2* __restrict__ dst, const double* __restrict__ mesh_cs,
+                                 const uint32_t* __restrict__ bnd_bits, const double2* __restrict__ fixed_xy) {
+    const int2 r = items[blockIdx.x];
+    const double* cs = mesh_cs + 4 * item_mesh[blockIdx.x];
+    for (int32_t k = r.x + threadIdx.x; k < r.y; k += blockDim.x) {
+        const int32_t o = new_to_old[k];
+        dst[o] = boundary_bit(bnd_bits, k) ? fixed_xy[o] : denormalise(src[k], cs[0], cs[1], cs[3]);
+    }
+}
+
+__global__ void k_div_selftest(int32_t count, const double* __restrict__ s, const int32_t* __restrict__ d,
+                               const double* __restrict__ recip, double* __restrict__ q) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) q[i] = div_by_count(s[i], d[i], recip);
+}
+
+inline unsigned blocks_for(int64_t count, int block) { return static_cast<unsigned>((count + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream) {
+    const int32_t count = a.v_end - a.v_begin;
+    if (count <= 0) return cudaSuccess;
+    const unsigned grid = blocks_for(count, block);
+    if (precision == LMS_FP64) {
+        if (in_place)
+            k_sweep<true, true><<<grid, block, 0, stream>>>(a);
+        else
+            k_sweep<true, false><<<grid, block, 0, stream>>>(a);
+    } else {
+        if (in_place)
+            k_sweep<false, true><<<grid, block, 0, stream>>>(a);
+        else
+            k_sweep<false, false><<<grid, block, 0, stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, cudaStream_t stream) {
+    switch (lanes) {
+        case 1: k_batch_sweep<1><<<grid, block, 0, stream>>>(a); break;
+        case 2: k_batch_sweep<2><<<grid, block, 0, stream>>>(a); break;
+        case 4: k_batch_sweep<4><<<grid, block, 0, stream>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int batch_sweep_occupancy(int block, int lanes) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (lanes) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<1>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<2>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<4>, block, 0); break;
+        default: break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
+                                     cudaStream_t stream) {
+    if (ntri <= 0) return cudaSuccess;
+    k_tri_quality_exact<<<blocks_for(ntri, 256), 256, 0, stream>>>(ntri, tri, reinterpret_cast<const double2*>(xy64),
+                                                                   q_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_quality_exact(int32_t n, const int32_t* vt_ptr, const int32_t* vt_idx, const double* q_t,
+                                        double* q_v, cudaStream_t stream) {
+    k_vertex_quality_exact<<<blocks_for(n, 256), 256, 0, stream>>>(n, vt_ptr, vt_idx, q_t, q_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quality_partials(int precision, int32_t ntri, const int32_t* tri, const void* xy, const double* w,
+                                    double* partials, const DevState* state, cudaStream_t stream) {
+    if (precision == LMS_FP64)
+        k_quality_partials<double2><<<kQualityBlocks, 256, 0, stream>>>(
+            ntri, tri, static_cast<const double2*>(xy), w, partials, state);
+    else
+        k_quality_partials<float2><<<kQualityBlocks, 256, 0, stream>>>(
+            ntri, tri, static_cast<const float2*>(xy), w, partials, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quality_finish(const double* partials, double n, DevState* state, int mode, cudaStream_t stream) {
+    k_quality_finish<<<1, kQualityBlocks, 0, stream>>>(partials, n, state, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stop_check(const double* partials, double n, DevState* state, double tol, double goal,
+                              int32_t max_iters, cudaStream_t stream) {
+    k_stop_check<<<1, kQualityBlocks, 0, stream>>>(partials, n, state, tol, goal, max_iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(int32_t n, const int32_t* new_to_old, const int32_t* rp_src, const int32_t* ci_src,
+                               const int32_t* rp_dst, int32_t* ci_dst, const int32_t* map, cudaStream_t stream) {
+    k_gather_rows<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, rp_src, ci_src, rp_dst, ci_dst, map);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_ids(int64_t count, const int32_t* map, const int32_t* src, int32_t* dst,
+                           cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_map_ids<<<blocks_for(count, 256), 256, 0, stream>>>(count, map, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_bits(int32_t n, const int32_t* new_to_old, const uint8_t* bnd_orig, uint32_t* bits,
+                                 cudaStream_t stream) {
+    k_boundary_bits<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, bnd_orig, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_xy(int precision, int32_t n, const int32_t* perm, const void* src, void* dst,
+                             cudaStream_t stream) {
+    if (precision == LMS_FP64)
+        k_gather_xy<double2><<<blocks_for(n, 256), 256, 0, stream>>>(n, perm, static_cast<const double2*>(src),
+                                                                     static_cast<double2*>(dst));
+    else
+        k_gather_xy<float2><<<blocks_for(n, 256), 256, 0, stream>>>(n, perm, static_cast<const float2*>(src),
+                                                                    static_cast<float2*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_xy(int precision, int32_t n, const int32_t* new_to_old, const double* src_orig, void* dst,
+                           double cx, double cy, double inv_s, cudaStream_t stream) {
+    const double2* src = reinterpret_cast<const double2*>(src_orig);
+    if (precision == LMS_FP64)
+        k_load_xy_f64<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, src, static_cast<double2*>(dst));
+    else
+        k_load_xy_f32<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, src, static_cast<float2*>(dst), cx, cy,
+                                                              inv_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_xy(int precision, int32_t n, const int32_t* new_to_old, const void* src, double* dst_orig,
+                            double cx, double cy, double s, const uint8_t* bnd_orig, const double* fixed_xy,
+                            cudaStream_t stream) {
+    double2* dst = reinterpret_cast<double2*>(dst_orig);
+    if (precision == LMS_FP64)
+        k_store_xy_f64<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, static_cast<const double2*>(src), dst);
+    else
+        k_store_xy_f32<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, static_cast<const float2*>(src), dst,
+                                                               cx, cy, s, bnd_orig,
+                                                               reinterpret_cast<const double2*>(fixed_xy));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_load_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
+                                 const int32_t* new_to_old, const double* src_orig, float2* dst,
+                                 const double* mesh_cs, cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    k_batch_load_xy<<<n_items, 256, 0, stream>>>(items, item_mesh, new_to_old,
+                                                 reinterpret_cast<const double2*>(src_orig), dst, mesh_cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
+                                  const int32_t* new_to_old, const float2* src, double* dst_orig,
+                                  const double* mesh_cs, const uint32_t* bnd_bits, const double* fixed_xy,
+                                  cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    k_batch_store_xy<<<n_items, 256, 0, stream>>>(items, item_mesh, new_to_old, src,
+                                                  reinterpret_cast<double2*>(dst_orig), mesh_cs, bnd_bits,
+                                                  reinterpret_cast<const double2*>(fixed_xy));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_div_selftest(int32_t count, const double* s, const int32_t* d, const double* recip, double* q,
+                                cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_div_selftest<<<blocks_for(count, 256), 256, 0, stream>>>(count, s, d, recip, q);
+    return cudaGetLastError();
+}
+
+}  // namespace lms

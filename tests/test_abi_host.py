@@ -1,0 +1,140 @@
+"""C ABI of liblms without a GPU: the library loads, exports every entry point
+that include/lms.h declares, and its host logic (validation, the four orderings
+and the colouring) matches the FP64 oracle bit for bit."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+import paper_1606_00803_gb300 as lms
+from conftest import ROOT
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "lms.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lms_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lms._lib()
+    names = declared_entry_points()
+    assert len(names) >= 30
+    nm = subprocess.run(["nm", "-D", "--defined-only", lms.library_path()], stdout=subprocess.PIPE, check=True)
+    exported = set(re.findall(r" T (lms_[a-z0-9_]+)", nm.stdout.decode()))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_error_strings():
+    lib = lms._lib()
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -99]:
+        s = lib.lms_error_string(code).decode()
+        assert s and isinstance(s, str)
+
+
+def _tiny():
+    return meshgen.workload(1, side=9)
+
+
+def test_validate_accepts_generated_meshes():
+    for side in (5, 16, 33):
+        m = meshgen.workload(1, side=side)
+        assert lms.validate(m["row_ptr"], m["col_idx"], m["is_boundary"], m["tri"]) == 0
+
+
+def test_validate_rejects_bad_meshes():
+    m = _tiny()
+    rp, ci, b, t = m["row_ptr"].copy(), m["col_idx"].copy(), m["is_boundary"].copy(), m["tri"].copy()
+    v = int(np.nonzero(b == 0)[0][0])
+    # out-of-range id
+    c2 = ci.copy(); c2[0] = len(rp) + 5
+    assert lms.validate(rp, c2, b, t) == -2
+    # self-loop
+    c2 = ci.copy(); c2[rp[v]] = v
+    assert lms.validate(rp, c2, b, t) == -2
+    # duplicate entry in a row
+    c2 = ci.copy(); c2[rp[v] + 1] = c2[rp[v]]
+    assert lms.validate(rp, c2, b, t) == -2
+    # asymmetric: replace one neighbour by a non-adjacent vertex
+    c2 = ci.copy()
+    row = set(ci[rp[v]:rp[v + 1]].tolist()) | {v}
+    far = next(u for u in range(len(rp) - 1) if u not in row)
+    c2[rp[v]] = far
+    assert lms.validate(rp, c2, b, t) == -2
+    # non-monotone offsets
+    r2 = rp.copy(); r2[3] = r2[4] + 1
+    assert lms.validate(r2, ci, b, t) == -2
+    # isolated interior vertex: a vertex with an empty row that is not on the boundary
+    n = len(rp) - 1
+    r3 = np.concatenate([rp, [rp[-1]]]).astype(np.int32)
+    b3 = np.concatenate([b, [0]]).astype(np.uint8)
+    assert lms.validate(r3, ci, b3, t) == -3
+    b3[-1] = 1   # a fixed vertex may be isolated
+    assert lms.validate(r3, ci, b3, t) == 0
+    # triangle with a repeated or out-of-range corner
+    t2 = t.copy(); t2[0, 1] = t2[0, 0]
+    assert lms.validate(rp, ci, b, t2) == -1
+    t2 = t.copy(); t2[0, 1] = n + 3
+    assert lms.validate(rp, ci, b, t2) == -1
+
+
+@pytest.mark.parametrize("side", [6, 20, 57])
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR])
+def test_host_ordering_matches_oracle(side, ordering):
+    m = meshgen.workload(1, side=side)
+    q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
+    want = oracle.order(m, ordering, seed=1234 + side, q_v=q)
+    got = lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], ordering, seed=1234 + side, q_v=q)
+    assert np.array_equal(got, want)
+
+
+def test_host_rdr_handles_ties_and_unreached_vertices():
+    import json
+    from conftest import GOLDEN
+    g = json.load(open(os.path.join(GOLDEN, "rdr_small.json")))
+    for case in g["cases"]:
+        got = lms.order_host(case["row_ptr"], case["col_idx"], case["is_boundary"], lms.RDR, q_v=case["q_v"])
+        assert got.tolist() == case["rdr_new_to_old"]
+    # all keys equal: ties fall back to vertex id in both implementations
+    m = meshgen.workload(1, side=15)
+    q = np.full(m["n"], 0.5)
+    assert np.array_equal(lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.RDR, q_v=q),
+                          oracle.order_rdr(m["row_ptr"], m["col_idx"], m["is_boundary"], q))
+
+
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR])
+def test_host_colouring_matches_oracle(ordering):
+    m = meshgen.workload(1, side=45)
+    p = oracle.order(m, ordering, seed=3)
+    c_want, n_want = oracle.color_greedy(m["row_ptr"], m["col_idx"], m["is_boundary"], p)
+    c_got, n_got = lms.color_host(m["row_ptr"], m["col_idx"], m["is_boundary"], p)
+    assert n_got == n_want and np.array_equal(c_got, c_want)
+
+
+def test_host_orderings_on_a_disconnected_mesh():
+    a, b = meshgen.workload(1, side=7), meshgen.workload(0, side=5)
+    n = a["n"] + b["n"]
+    rp = np.concatenate([a["row_ptr"], b["row_ptr"][1:] + a["row_ptr"][-1]]).astype(np.int32)
+    ci = np.concatenate([a["col_idx"], b["col_idx"] + a["n"]]).astype(np.int32)
+    bnd = np.concatenate([a["is_boundary"], b["is_boundary"]])
+    tri = np.concatenate([a["tri"], b["tri"] + a["n"]])
+    xy = np.concatenate([a["xy"], b["xy"] + 3.0])
+    m = dict(n=n, row_ptr=rp, col_idx=ci, is_boundary=bnd, tri=tri, xy=xy)
+    q = oracle.vertex_quality(n, tri, xy)
+    for ordering in (lms.BFS, lms.RDR, lms.RANDOM):
+        assert np.array_equal(lms.order_host(rp, ci, bnd, ordering, seed=9, q_v=q), oracle.order(m, ordering, 9, q))
+
+
+def test_host_entry_points_reject_bad_arguments():
+    m = _tiny()
+    with pytest.raises(lms.LmsError):
+        lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], 7)
+    with pytest.raises(lms.LmsError):
+        lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.RDR, q_v=None)

@@ -1,0 +1,123 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configuration
+the benchmark times (autotuned, shared through the autotune cache).
+
+Where the oracle would take minutes, outputs are sampled (whole meshes of the
+512-mesh batch; fewer sweeps on the 4096 x 4096 mesh) and the rest is checked
+through properties that hold at any size: boundary vertices unchanged, every
+position finite and inside its mesh's bounding box (Eq. 1 is a convex
+combination), permutations bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+import paper_1606_00803_gb300 as lms
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 2e-6
+
+
+def diag(m):
+    xy = m["xy"]
+    return math.hypot(np.ptp(xy[:, 0]), np.ptp(xy[:, 1]))
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return meshgen.workload(1)
+
+
+def test_workload1_fp64_rdr_jacobi_100_bit_exact(w1):
+    m = w1
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 100)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(lms.RDR)
+        assert np.array_equal(g.permutation(), oracle.order(m, oracle.RDR))
+        g.smooth(100)
+        got = g.coords()
+    assert np.abs(got - want).max() <= TOL64 * diag(m)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ordering", [lms.RANDOM, lms.RDR])
+def test_workload1_fp32_jacobi_100(w1, ordering):
+    m = w1
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 100)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(ordering, seed=meshgen.BASE_SEED + 7)
+        g.smooth(100)
+        got = g.coords()
+    assert np.abs(got - want).max() <= TOL32 * diag(m)
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_workload1_coloured_gs_bfs(w1, precision):
+    m = w1
+    p = oracle.order(m, oracle.BFS)
+    want, _, _ = oracle.gs_smooth(m, p, 20)
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.BFS)
+        g.smooth(20, mode=lms.COLORED_GS)
+        got = g.coords()
+    if precision == lms.FP64:
+        assert np.array_equal(got, want)
+    else:
+        assert np.abs(got - want).max() <= TOL32 * diag(m)
+
+
+def test_workload2_graded_fp32_and_stopping_rule():
+    m = meshgen.workload(2)
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 40)
+    Q0 = oracle.mesh_quality(m["n"], m["tri"], m["xy"])
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.RDR)
+        g.smooth(40)
+        assert np.abs(g.coords() - want).max() <= TOL32 * diag(m)
+        g.set_coords(m["xy"])
+        k = g.smooth(200, tol=5e-6)
+        st = g.last_stats()
+    assert 1 <= k <= 200
+    assert abs(st["q_first"] - Q0) <= 1e-6
+    assert st["q_last"] > st["q_first"]
+
+
+def test_workload4_max_size_sampled():
+    m = meshgen.workload(4)
+    sweeps = 6
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(lms.RDR)
+        g.smooth(sweeps)
+        assert np.array_equal(g.coords(), want)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.RANDOM, seed=1)
+        g.smooth(sweeps)
+        assert np.abs(g.coords() - want).max() <= TOL32 * diag(m)
+
+
+def test_workload3_batched_full_size_sampled():
+    meshes = meshgen.batch_workload()
+    with lms.Batch(meshes, ordering=lms.RDR) as b:
+        b.autotune()
+        b.smooth(50)
+        allc = b.all_coords()
+        sizes = [m["n"] for m in meshes]
+        sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 0, 511, 100, 257, 333, 404})
+        for i in sample:
+            m = meshes[i]
+            assert np.array_equal(b.permutation(i), oracle.order(m, oracle.RDR))
+            want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 50)
+            assert np.abs(b.coords(i) - want).max() <= TOL32 * diag(m)
+    off = 0
+    for m in meshes:
+        x = allc[off:off + m["n"]]
+        off += m["n"]
+        bd = m["is_boundary"] == 1
+        assert np.isfinite(x).all()
+        assert np.array_equal(x[bd], m["xy"][bd])
+        lo, hi = m["xy"].min(axis=0), m["xy"].max(axis=0)
+        assert (x >= lo - 1e-6).all() and (x <= hi + 1e-6).all()

@@ -1,0 +1,329 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 max |dx| <= 1e-12 x bounding-box diagonal (and bit-exact
+where the design promises it: Jacobi and coloured GS keep the oracle's
+summation order and use a correctly rounded division); FP32 with normalised
+coordinates and Kahan sums <= 2e-6 x diagonal after up to 200 sweeps;
+permutations, colourings and relabelled CSR bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+import paper_1606_00803_gb300 as lms
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-6
+ORDERINGS = [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR]
+
+
+def diag(m):
+    xy = m["xy"]
+    return math.hypot(xy[:, 0].max() - xy[:, 0].min(), xy[:, 1].max() - xy[:, 1].min())
+
+
+def err(a, b, m):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / diag(m)
+
+
+@pytest.fixture(scope="module")
+def mesh_mid():
+    # ~10.5k vertices: many 256-thread blocks and a ragged last block
+    return meshgen.workload(1, side=100)
+
+
+@pytest.fixture(scope="module")
+def mesh_graded():
+    return meshgen.workload(2, side=70)
+
+
+def test_division_selftest_matches_ieee():
+    rng = np.random.default_rng(0)
+    d = rng.integers(1, 80, size=2_000_000).astype(np.int32)
+    s = rng.uniform(-8, 8, size=d.size) * np.exp2(rng.integers(-30, 30, size=d.size))
+    # neighbour sums of positions: also exact multiples and values near them
+    s[:1000] = np.arange(1000) * 3.0
+    s[1000:2000] = np.nextafter(np.arange(1000) * 7.0, np.inf)
+    s[2000:3000] = 0.0
+    q = lms.selftest_div64(s, d)
+    assert np.array_equal(q, s / d)
+
+
+def test_config0_fp64_jacobi_bit_exact():
+    m = meshgen.workload(0)
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 10)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        assert g.smooth(10) == 10
+        got = g.coords()
+    assert err(got, want, m) <= TOL64
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ordering", ORDERINGS)
+def test_fp64_jacobi_all_orderings(mesh_mid, ordering):
+    m = mesh_mid
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 37)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(ordering, seed=77)
+        assert np.array_equal(g.permutation(), oracle.order(m, ordering, seed=77))
+        g.smooth(37)
+        got = g.coords()
+    assert err(got, want, m) <= TOL64
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ordering", ORDERINGS)
+def test_fp32_jacobi_all_orderings(mesh_mid, ordering):
+    m = mesh_mid
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 100)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(ordering, seed=5)
+        g.smooth(100)
+        got = g.coords()
+    assert err(got, want, m) <= TOL32
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+@pytest.mark.parametrize("ordering", ORDERINGS)
+def test_coloured_gs_equals_inplace_sweep_in_colour_order(mesh_mid, precision, ordering):
+    m = mesh_mid
+    p = oracle.order(m, ordering, seed=11)
+    want, _, _ = oracle.gs_smooth(m, p, 25)
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(ordering, seed=11)
+        g.smooth(25, mode=lms.COLORED_GS)
+        got = g.coords()
+        colour, nc = g.colors()
+    c_want, nc_want = oracle.color_greedy(m["row_ptr"], m["col_idx"], m["is_boundary"], p)
+    assert nc == nc_want and np.array_equal(colour, c_want)
+    if precision == lms.FP64:
+        assert err(got, want, m) <= TOL64
+        assert np.array_equal(got, want)
+    else:
+        assert err(got, want, m) <= TOL32
+
+
+@pytest.mark.parametrize("ordering", ORDERINGS)
+def test_relabelled_csr_matches_oracle(mesh_graded, ordering):
+    m = mesh_graded
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(ordering, seed=2)
+        rp, ci, storage = g.csr()
+        p = g.permutation()
+    assert np.array_equal(p, oracle.order(m, ordering, seed=2))
+    assert np.array_equal(storage, p)
+    rp_w, ci_w = oracle.relabel(m["row_ptr"], m["col_idx"], p)
+    assert np.array_equal(rp, rp_w) and np.array_equal(ci, ci_w)
+
+
+def test_coloured_layout_csr(mesh_graded):
+    m = mesh_graded
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.RDR)
+        g.smooth(1, mode=lms.COLORED_GS)
+        rp, ci, storage = g.csr()
+        colour, nc = g.colors()
+        p = g.permutation()
+    seq = oracle.color_sequence(m["is_boundary"], p, colour, nc)
+    assert np.array_equal(storage[: len(seq)], seq)
+    rp_w, ci_w = oracle.relabel(m["row_ptr"], m["col_idx"], storage)
+    assert np.array_equal(rp, rp_w) and np.array_equal(ci, ci_w)
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_quality_matches_oracle(mesh_graded, precision):
+    m = mesh_graded
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.RDR)
+        q0 = g.quality()
+        g.smooth(20)
+        q1 = g.quality()
+        x = g.coords()
+    w0 = oracle.mesh_quality(m["n"], m["tri"], m["xy"])
+    w1 = oracle.mesh_quality(m["n"], m["tri"], x)
+    tol = 1e-13 if precision == lms.FP64 else 1e-6
+    assert abs(q0 - w0) <= tol and abs(q1 - w1) <= tol
+    assert q1 > q0
+
+
+@pytest.mark.parametrize("mode", [lms.JACOBI, lms.COLORED_GS])
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_stopping_rule_matches_oracle(mesh_graded, mode, precision):
+    m = mesh_graded
+    tol = 5e-6
+    p = oracle.order(m, oracle.RDR)
+    if mode == lms.JACOBI:
+        _, k_or, hist = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 200, tri=m["tri"], tol=tol)
+    else:
+        _, k_or, hist = oracle.gs_smooth(m, p, 200, tol=tol)
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.RDR)
+        k = g.smooth(200, mode=mode, tol=tol)
+        got = g.coords()
+        st = g.last_stats()
+    assert 1 <= k <= 200
+    if precision == lms.FP64:
+        near = np.abs(np.diff(hist) - tol) < 1e-9
+        assert k == k_or or near[min(k, k_or) - 1]
+    # compare positions with the oracle run for the GPU's sweep count
+    if mode == lms.JACOBI:
+        want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], k)
+    else:
+        want, _, _ = oracle.gs_smooth(m, p, k)
+    assert err(got, want, m) <= (TOL64 if precision == lms.FP64 else TOL32)
+    assert abs(st["q_first"] - hist[0]) < (1e-13 if precision == lms.FP64 else 1e-6)
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_boundary_fixed_and_displacement(mesh_mid, precision):
+    m = mesh_mid
+    b = m["is_boundary"] == 1
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.BFS)
+        g.smooth(30)
+        x30 = g.coords()
+        g.smooth(1)
+        x31 = g.coords()
+        st = g.last_stats()
+    assert np.array_equal(x31[b], m["xy"][b])  # FP32 returns the stored FP64 boundary values
+    want = np.sqrt(((x31 - x30) ** 2).sum(axis=1)).max()
+    assert abs(st["max_disp"] - want) <= (1e-15 if precision == lms.FP64 else 1e-6) * diag(m) + 1e-12 * want
+    assert st["ms"] > 0
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_checkpoint_resume_is_exact(mesh_mid, precision):
+    # 40 + 40 sweeps through get/set of FP64 positions equals 80 sweeps (FP64 exactly; FP32 within
+    # one normalisation round trip per checkpoint)
+    m = mesh_mid
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.RDR)
+        g.smooth(80)
+        full = g.coords()
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.RDR)
+        g.smooth(40)
+        mid = g.coords()
+        g.set_coords(mid)
+        g.smooth(40)
+        resumed = g.coords()
+    if precision == lms.FP64:
+        assert np.array_equal(full, resumed)
+    else:
+        assert err(full, resumed, m) <= TOL32
+
+
+def test_fp32_error_report_after_200_sweeps(mesh_graded):
+    m = mesh_graded
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 200)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.RDR)
+        g.smooth(200)
+        got = g.coords()
+    assert err(got, want, m) <= TOL32
+
+
+def test_uniform_grid_fixed_point_on_gpu():
+    s = 33
+    h = 1.0 / 32
+    xy = np.array([[i * h, j * h] for j in range(s) for i in range(s)])
+    bnd = np.array([1 if (i in (0, s - 1) or j in (0, s - 1)) else 0 for j in range(s) for i in range(s)], np.uint8)
+    adj = [set() for _ in range(s * s)]
+    for j in range(s):
+        for i in range(s):
+            v = j * s + i
+            for di, dj in ((1, 0), (0, 1), (1, 1)):
+                if i + di < s and j + dj < s:
+                    u = (j + dj) * s + i + di
+                    adj[v].add(u)
+                    adj[u].add(v)
+    rp = np.cumsum([0] + [len(a) for a in adj]).astype(np.int32)
+    ci = np.concatenate([sorted(a) for a in adj]).astype(np.int32)
+    for precision in (lms.FP64, lms.FP32):
+        with lms.Mesh(rp, ci, xy, bnd, precision=precision) as g:
+            g.reorder(lms.RANDOM, seed=1)
+            g.smooth(10)
+            got = g.coords()
+            g.smooth(3, mode=lms.COLORED_GS)
+            got2 = g.coords()
+        assert np.array_equal(got, xy) and np.array_equal(got2, xy)
+
+
+def test_api_errors():
+    m = meshgen.workload(0, side=10)
+    with pytest.raises(lms.LmsError) as e:
+        lms.Mesh(m["row_ptr"], m["col_idx"][::-1].copy(), m["xy"], m["is_boundary"], m["tri"])
+    assert e.value.status == -2
+    with lms.Mesh(m["row_ptr"], m["col_idx"], m["xy"], m["is_boundary"], None) as g:
+        with pytest.raises(lms.LmsError) as e:
+            g.reorder(lms.RDR)
+        assert e.value.status == -4
+        with pytest.raises(lms.LmsError) as e:
+            g.smooth(5, tol=1e-6)
+        assert e.value.status == -4
+        with pytest.raises(lms.LmsError) as e:
+            g.smooth(5, mode=9)
+        assert e.value.status == -1
+        g.smooth(0)
+        assert np.array_equal(g.coords(), m["xy"])
+    bad = m["xy"].copy()
+    bad[3, 0] = np.nan
+    with pytest.raises(lms.LmsError):
+        lms.Mesh(m["row_ptr"], m["col_idx"], bad, m["is_boundary"], m["tri"])
+
+
+# ------------------------------------------------------------------- batched
+
+
+def small_batch(count=10):
+    sides = [12, 13, 17, 20, 25, 31, 40, 47, 55, 64][:count]
+    return [meshgen.generate(s, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=1000 + i)
+            for i, s in enumerate(sides)]
+
+
+@pytest.mark.parametrize("config", [(256, 1, 256), (512, 2, 1024), (128, 4, 512), (256, 1, 4096)])
+def test_batched_fp32_matches_oracle(config):
+    meshes = small_batch()
+    with lms.Batch(meshes, ordering=lms.RDR) as b:
+        b.set_config(*config)
+        b.smooth(50)
+        for i, m in enumerate(meshes):
+            assert np.array_equal(b.permutation(i), oracle.order(m, oracle.RDR))
+            want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 50)
+            assert err(b.coords(i), want, m) <= TOL32
+        allc = b.all_coords()
+        assert np.array_equal(allc[b.offsets[3]:b.offsets[4]], b.coords(3))
+
+
+def test_batched_autotune_keeps_positions():
+    meshes = small_batch(6)
+    with lms.Batch(meshes, ordering=lms.BFS) as b:
+        before = b.all_coords()
+        cfg = b.autotune()
+        assert cfg["block"] in (128, 256, 512) and cfg["lanes"] in (1, 2, 4)
+        assert np.array_equal(b.all_coords(), before)
+        b.smooth(7)
+        b.smooth(8)
+        got = b.all_coords()
+    for i, m in enumerate(meshes):
+        want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 15)
+        assert err(got[sum(len(x["xy"]) for x in meshes[:i]):][: m["n"]], want, m) <= TOL32
+
+
+def test_batched_set_coords_round_trip():
+    meshes = small_batch(4)
+    with lms.Batch(meshes, ordering=lms.RANDOM, seed=3) as b:
+        xy = np.concatenate([m["xy"] for m in meshes])
+        b.smooth(20)
+        b.set_all_coords(xy)
+        b.smooth(20)
+        got = b.all_coords()
+    for i, m in enumerate(meshes):
+        want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 20)
+        o = sum(x["n"] for x in meshes[:i])
+        assert err(got[o:o + m["n"]], want, m) <= TOL32
