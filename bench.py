@@ -264,6 +264,18 @@ def per_ordering_table(hbm_peak):
                     row["fp64_ops_per_s"] = ops
                 rows["%s/%s/%s" % (oname, pname, mname)] = row
             rows["%s/%s/reorder_ms" % (oname, pname)] = round(reorder_ms, 1)
+            if o == lms.RDR:
+                # the tile-staged kernel on the same mesh, for comparison
+                g.reorder(o)
+                g.set_launch(lms.KERNEL_STAGED, 256, 256 if p == lms.FP64 else 512)
+                g.smooth(PER_ORDERING_SWEEPS)
+                torch.cuda.synchronize()
+                ms = min(time_graph(lambda: g.smooth(PER_ORDERING_SWEEPS), stream, 1) for _ in range(3))
+                sweep_ms = ms / PER_ORDERING_SWEEPS
+                ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
+                rows["%s/%s/jacobi_staged" % (oname, pname)] = dict(
+                    updates_per_s=n_int / (sweep_ms * 1e-3), sweep_ms=round(sweep_ms, 5),
+                    algorithmic_gbs=round(ab / (sweep_ms * 1e-3) / 1e9, 1))
             g.close()
     return dict(workload="1024x1024 jittered grid + 10%% flips + 5%% splits (%d vertices, %d interior, %d CSR "
                          "entries), %d sweeps; working set fits in L2 at FP32, so GB/s may exceed HBM" %
@@ -408,7 +420,8 @@ def run_ours(args, dist):
                 "launch": cfg, "parallelism": "each rank smooths its own batch" if dist.world > 1 else "1 GPU",
                 "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_batch_sweep<%d>" % cfg["lanes"],
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": ("k_sweep_staged<fp32>" if cfg["kernel"] == lms.KERNEL_STAGED
+                                    else "k_batch_sweep<%d>" % cfg["lanes"]),
                          "algorithmic_bytes_per_launch": ab, "launch_ms": sweep_ms,
                          "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 7900.0},
             "cpu_baseline": cpu,

@@ -68,6 +68,14 @@ extern "C" {
                             in storage order; equals Algorithm 1's sequential in-place sweep taken in
                             (colour, storage position) order */
 
+/* sweep kernels */
+#define LMS_KERNEL_DIRECT 0 /* thread (or 2/4 lanes) per vertex, CSR and positions loaded through L1 */
+#define LMS_KERNEL_STAGED 1 /* tile CSR brought to shared memory by TMA bulk copies one tile ahead; neighbour
+                               positions gathered edge-parallel into shared memory, then summed per vertex */
+#define LMS_KERNEL_SELL 2   /* batched only: SELL-C-sigma work layout - inside every tile the interior vertices
+                               sorted by degree into slices of 32 whose neighbour ids are stored
+                               column-major; one lane per slot, coalesced id loads, no row offsets */
+
 typedef struct lms_mesh_s* lms_handle;
 typedef struct lms_batch_s* lms_batch;
 
@@ -150,6 +158,14 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed);
  */
 int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done);
 
+/*
+ * Sweep kernel of a handle: LMS_KERNEL_DIRECT (default; one thread per vertex, rows read 4 entries at a
+ * time; tile ignored) or LMS_KERNEL_STAGED (tile = vertices per work item, a multiple of 32 up to 4096;
+ * the handle's initial tile is 512 for FP32 and 256 for FP64); block = 128 or 256 threads.  Results do not
+ * depend on the choice.
+ */
+int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
+
 /* Global mesh quality Q (Section 3.2, FP64 reduction) of the current coordinates. */
 int lms_quality(lms_handle h, double* Q);
 
@@ -206,29 +222,42 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
 /* `iters` Jacobi sweeps of every mesh, recorded once into a CUDA graph and replayed (asynchronous). */
 int lms_batch_smooth(lms_batch b, int32_t iters);
 
-/* Coordinates of mesh `mesh` in its original labelling ([2 n_mesh] doubles). */
+/* Coordinates of mesh `mesh` in its original labelling ([2 n_mesh] doubles).  Returns LMS_ERR_TIMEOUT
+   when a sweep since the batch's creation gave up a bounded wait (its results are then unreliable). */
 int lms_batch_get_coords(lms_batch b, int32_t mesh, double* xy);
 
 /* All meshes' coordinates, concatenated in mesh order, original labelling ([2 sum n] doubles). */
 int lms_batch_get_all_coords(lms_batch b, double* xy);
 
-/* Replace all meshes' coordinates (concatenated as above); the orderings are kept. */
+/* Replace all meshes' coordinates (concatenated as above); the orderings are kept.  Asynchronous: xy must
+   stay valid until the stream has read it, and a non-finite value is reported as LMS_ERR_ARG by the next
+   lms_batch_get_coords / lms_batch_get_all_coords. */
 int lms_batch_set_all_coords(lms_batch b, const double* xy);
 
 /* Totals: vertices, interior vertices, CSR entries, tiles (any pointer may be NULL). [no device work] */
 int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles);
 
 /*
- * Launch configuration of the batched sweep: block = threads per CTA,
- * lanes = lanes per vertex (1, 2 or 4), tile = vertices per work item,
- * ctas_per_sm = resident CTAs the persistent grid assumes.
- * lms_batch_autotune times the candidates on the batch (without changing its
- * coordinates), keeps the fastest, and returns it; results are cached in the
- * file named by the LMS_AUTOTUNE_CACHE environment variable when it is set.
+ * Launch configuration of the batched sweep: kernel = LMS_KERNEL_* (SELL: tile
+ * = sorting window sigma, lanes 1 / -4 / -8, halo 0), block =
+ * threads per CTA (128/256/512; staged: 128 or 256), lanes = lanes per vertex
+ * (1, 2 or 4), or -4 / -8 for one lane per vertex reading its row 4 / 8
+ * entries at a time (all ids, then all gathers, then the sums; staged: 1), tile = vertices per work item (multiple of 128;
+ * staged: at most 4096), halo = direct kernel with one lane per vertex: the
+ * positions of [tile start - halo, tile end + halo) are staged in shared
+ * memory and in-window neighbours read from there (0 = off; lanes > 1 and
+ * staged: 0),
+ * ctas_per_sm = resident CTAs of the persistent grid (0 = as many as fit).  lms_batch_autotune times the candidates on the batch
+ * (without changing its coordinates), keeps the fastest and returns it;
+ * results are cached in the file named by the LMS_AUTOTUNE_CACHE environment
+ * variable when it is set.  Any output pointer may be NULL.
  */
-int lms_batch_get_config(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm);
-int lms_batch_set_config(lms_batch b, int32_t block, int32_t lanes, int32_t tile, int32_t ctas_per_sm);
-int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm);
+int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile,
+                         int32_t* halo, int32_t* ctas_per_sm);
+int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t lanes, int32_t tile, int32_t halo,
+                         int32_t ctas_per_sm);
+int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* halo,
+                       int32_t* ctas_per_sm);
 
 /* Ordering of mesh `mesh` of a batch ([n_mesh] new_to_old, local ids).  LMS_RANDOM uses seed + mesh. */
 int lms_batch_get_permutation(lms_batch b, int32_t mesh, int32_t* new_to_old);

@@ -22,6 +22,7 @@ import numpy as np
 from . import _build
 
 FP64, FP32 = 0, 1
+KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
 ORI, RANDOM, BFS, RDR = 0, 1, 2, 3
 JACOBI, COLORED_GS = 0, 1
 ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR}
@@ -68,6 +69,7 @@ _SIGS = {
     "lms_reorder": ([_P, ctypes.c_int, _U64], ctypes.c_int),
     "lms_smooth": ([_P, _I32, ctypes.c_int, _D, _PI32], ctypes.c_int),
     "lms_quality": ([_P, _PD], ctypes.c_int),
+    "lms_set_launch": ([_P, _I32, _I32, _I32], ctypes.c_int),
     "lms_get_coords": ([_P, _P], ctypes.c_int),
     "lms_set_coords": ([_P, _P], ctypes.c_int),
     "lms_get_permutation": ([_P, _P], ctypes.c_int),
@@ -83,9 +85,9 @@ _SIGS = {
     "lms_batch_get_all_coords": ([_P, _P], ctypes.c_int),
     "lms_batch_set_all_coords": ([_P, _P], ctypes.c_int),
     "lms_batch_info": ([_P, _PI64, _PI64, _PI64, _PI32], ctypes.c_int),
-    "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
-    "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32], ctypes.c_int),
-    "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
+    "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
     "lms_batch_get_permutation": ([_P, _I32, _P], ctypes.c_int),
     "lms_batch_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_batch_destroy": ([_P], None),
@@ -263,6 +265,9 @@ class Mesh:
                "lms_smooth")
         return done.value
 
+    def set_launch(self, kernel, block=256, tile=512):
+        _check(_lib().lms_set_launch(self._handle(), kernel, block, tile), "lms_set_launch")
+
     def quality(self):
         q = ctypes.c_double()
         _check(_lib().lms_quality(self._handle(), ctypes.byref(q)), "lms_quality")
@@ -383,18 +388,21 @@ class Batch:
                                      ctypes.byref(tiles)), "lms_batch_info")
         return dict(n_total=n.value, n_interior=ni.value, nnz_total=nnz.value, tiles=tiles.value)
 
-    def config(self):
-        v = [ctypes.c_int32() for _ in range(4)]
-        _check(_lib().lms_batch_get_config(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_get_config")
-        return dict(block=v[0].value, lanes=v[1].value, tile=v[2].value, ctas_per_sm=v[3].value)
+    _CFG = ("kernel", "block", "lanes", "tile", "halo", "ctas_per_sm")
 
-    def set_config(self, block, lanes, tile, ctas_per_sm=0):
-        _check(_lib().lms_batch_set_config(self._handle(), block, lanes, tile, ctas_per_sm), "lms_batch_set_config")
+    def config(self):
+        v = [ctypes.c_int32() for _ in range(6)]
+        _check(_lib().lms_batch_get_config(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_get_config")
+        return dict(zip(self._CFG, [x.value for x in v]))
+
+    def set_config(self, kernel, block, lanes, tile, halo=0, ctas_per_sm=0):
+        _check(_lib().lms_batch_set_config(self._handle(), kernel, block, lanes, tile, halo, ctas_per_sm),
+               "lms_batch_set_config")
 
     def autotune(self):
-        v = [ctypes.c_int32() for _ in range(4)]
+        v = [ctypes.c_int32() for _ in range(6)]
         _check(_lib().lms_batch_autotune(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_autotune")
-        return dict(block=v[0].value, lanes=v[1].value, tile=v[2].value, ctas_per_sm=v[3].value)
+        return dict(zip(self._CFG, [x.value for x in v]))
 
     def last_launches(self):
         k = ctypes.c_int64()

@@ -247,6 +247,19 @@ struct lms_mesh_s {
     DevState* d_state = nullptr;
     DevState* h_state = nullptr;        // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // sweep launch configuration and tile tables (staged kernel)
+    int kernel = LMS_KERNEL_DIRECT, block = 256, tile = 512;
+    std::vector<int32_t> rp_cur;        // row offsets of the current layout (host copy)
+    int4* d_items4 = nullptr;           // tiles over [0, n), then tiles of each colour range
+    int64_t items_cap = 0;
+    int32_t n_items_all = 0;
+    std::vector<int32_t> item_col_ofs;  // colour c: tiles [n_items_all + ofs[c], n_items_all + ofs[c+1])
+    int32_t e_cap = 0;
+    int32_t* d_queue = nullptr;         // one tile counter per staged launch of a graph
+    int32_t queue_slots = 0;
+    int32_t slot_next = 0;              // next counter while a graph is recorded
+    int32_t* d_err = nullptr;           // set by a kernel whose bounded wait expired
+    int sms = 0;
     GraphCache graphs;
     int64_t last_launches = 0;
     bool stats_pending = false;
@@ -298,9 +311,53 @@ int apply_layout(lms_mesh_s* h, const std::vector<int32_t>& perm_new) {
     // the host vectors above must outlive the asynchronous copies
     LMS_CUDA(cudaStreamSynchronize(s));
     h->perm = perm_new;
+    h->rp_cur.swap(rp);
     h->graphs.clear();
     return LMS_OK;
 }
+
+// Tile tables of the current layout: tiles of `tile` vertices over [0, n) (Jacobi), then, in the
+// coloured layout, tiles over each colour's range (one coloured-GS launch per colour).
+int build_items(lms_mesh_s* h) {
+    std::vector<int4> items;
+    int32_t e_cap = 0;
+    auto add = [&](int32_t lo, int32_t hi) {
+        for (int32_t v = lo; v < hi; v += h->tile) {
+            const int32_t vb = std::min(hi, v + h->tile);
+            items.push_back(make_int4(v, vb, h->rp_cur[v], h->rp_cur[vb]));
+            e_cap = std::max(e_cap, h->rp_cur[vb] - h->rp_cur[v]);
+        }
+    };
+    add(0, h->n);
+    h->n_items_all = int32_t(items.size());
+    h->item_col_ofs.assign(1, 0);
+    if (h->coloured_layout)
+        for (int32_t c = 0; c < h->ncolours; ++c) {
+            add(h->colour_ofs[c], h->colour_ofs[c + 1]);
+            h->item_col_ofs.push_back(int32_t(items.size()) - h->n_items_all);
+        }
+    if (int64_t(items.size()) > h->items_cap) {
+        const int64_t cap = int64_t(items.size()) + 64;
+        LMS_TRY(h->arena.get(&h->d_items4, cap));
+        h->items_cap = cap;
+    }
+    LMS_CUDA(cudaMemcpyAsync(h->d_items4, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));
+    h->e_cap = e_cap;
+    h->graphs.clear();
+    return LMS_OK;
+}
+
+int ensure_queue(lms_mesh_s* h, int32_t slots) {
+    if (slots <= h->queue_slots) return LMS_OK;
+    const int32_t want = std::max<int32_t>(slots, 256);
+    LMS_TRY(h->arena.get(&h->d_queue, want));
+    h->queue_slots = want;
+    return LMS_OK;
+}
+
+int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_JACOBI ? 1 : h->ncolours; }
 
 // Current positions as FP64 in the original labelling, in d_xy64.
 int positions_fp64_original(lms_mesh_s* h) {
@@ -343,7 +400,7 @@ int ensure_coloured_layout(lms_mesh_s* h) {
     }
     LMS_TRY(apply_layout(h, p));
     h->coloured_layout = true;
-    return LMS_OK;
+    return build_items(h);
 }
 
 SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
@@ -363,11 +420,45 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
 // base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
 int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
     const int src = (base + k1 - 1) & 1;
+    if (h->kernel == LMS_KERNEL_STAGED) {
+        lms::StagedArgs a{};
+        a.row_ptr = h->d_rp;
+        a.col_idx = h->d_ci;
+        a.recip = h->d_recip;
+        a.err = h->d_err;
+        a.tile_cap = h->tile;
+        a.e_cap = h->e_cap;
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        const int occ = std::max(1, lms::staged_occupancy(h->precision, mode != LMS_JACOBI, h->block, h->tile, h->e_cap));
+        const int ranges = mode == LMS_JACOBI ? 1 : h->ncolours;
+        for (int32_t c = 0; c < ranges; ++c) {
+            if (mode == LMS_JACOBI) {
+                a.bnd_bits = h->d_bits;
+                a.src = h->d_xy[src];
+                a.dst = h->d_xy[src ^ 1];
+                a.items = h->d_items4;
+                a.n_items = h->n_items_all;
+            } else {
+                a.bnd_bits = nullptr;  // every vertex of a colour range is interior
+                a.src = h->d_xy[base];
+                a.dst = h->d_xy[base];
+                a.items = h->d_items4 + h->n_items_all + h->item_col_ofs[c];
+                a.n_items = h->item_col_ofs[c + 1] - h->item_col_ofs[c];
+            }
+            if (h->slot_next >= h->queue_slots) return LMS_ERR_STATE;
+            a.queue = h->d_queue + h->slot_next++;
+            const int grid = std::max(1, std::min(occ * h->sms, a.n_items));
+            LMS_TRY(check_launch(lms::launch_sweep_staged(h->precision, mode != LMS_JACOBI, a, grid, h->block, s),
+                                 "staged_sweep"));
+        }
+        return LMS_OK;
+    }
     if (mode == LMS_JACOBI) {
         SweepArgs a = sweep_args(h, src, src ^ 1);
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
-        return check_launch(lms::launch_sweep(h->precision, false, a, 256, s), "sweep");
+        return check_launch(lms::launch_sweep(h->precision, false, a, h->block, s), "sweep");
     }
     for (int32_t c = 0; c < h->ncolours; ++c) {
         SweepArgs a = sweep_args(h, base, base);
@@ -376,7 +467,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.v_end = h->colour_ofs[c + 1];
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
-        LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, 256, s), "sweep"));
+        LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, h->block, s), "sweep"));
     }
     return LMS_OK;
 }
@@ -405,11 +496,13 @@ int finish_stats(lms_mesh_s* h) {
     h->last_disp = std::sqrt(d2) * (h->precision == LMS_FP32 ? h->scale : 1.0);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->last_ms = ms;
-    if (st.err != 0) {
-        h->stats_pending = false;
+    int32_t kerr = 0;
+    LMS_CUDA(cudaMemcpy(&kerr, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    h->stats_pending = false;
+    if (st.err != 0 || kerr != 0) {
+        lms::set_error_detail("a bounded wait on a tile copy expired");
         return LMS_ERR_TIMEOUT;
     }
-    h->stats_pending = false;
     return LMS_OK;
 }
 
@@ -482,9 +575,9 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     int rc = LMS_OK;
     if ((rc = A.get(&h->d_rp0, n + 1)) || (rc = A.get(&h->d_ci0, std::max(1, h->nnz))) ||
         (rc = A.get(&h->d_tri0, t3)) || (rc = A.get(&h->d_vt_ptr, n + 1)) || (rc = A.get(&h->d_vt_idx, t3)) ||
-        (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1)) ||
-        (rc = A.get(&h->d_ci, std::max(1, h->nnz))) || (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
-        (rc = A.get(&h->d_tmp, n)) || (rc = A.get(&h->d_bits, (n + 31) / 32 + 4)) ||
+        (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1 + 8)) ||
+        (rc = A.get(&h->d_ci, h->nnz + 8)) || (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
+        (rc = A.get(&h->d_tmp, n)) || (rc = A.get(&h->d_bits, (n + 31) / 32 + 8)) || (rc = A.get(&h->d_err, 1)) ||
         (rc = A.get(&h->d_xy[0], vb)) || (rc = A.get(&h->d_xy[1], vb)) || (rc = A.get(&h->d_xy_swap, vb)) ||
         (rc = A.get(&h->d_xy64, 2 * size_t(n))) || (rc = A.get(&h->d_qt, std::max(1, ntri))) ||
         (rc = A.get(&h->d_qv, n)) || (rc = A.get(&h->d_partials, lms::kQualityBlocks)) ||
@@ -505,7 +598,9 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
         up(h->d_w, w.data(), 8 * size_t(ntri)) || up(h->d_recip, recip.data(), 8 * recip.size()) ||
         up(h->d_perm, ident.data(), 4 * size_t(n)) || up(h->d_rp, h->rp.data(), 4 * size_t(n + 1)) ||
         up(h->d_ci, h->ci.data(), 4 * size_t(h->nnz)) || up(h->d_tri, h->tri.data(), 12 * size_t(ntri)) ||
-        up(h->d_xy64, xy, 16 * size_t(n)) || cudaMemsetAsync(h->d_state, 0, sizeof(DevState), s)) {
+        up(h->d_xy64, xy, 16 * size_t(n)) || cudaMemsetAsync(h->d_state, 0, sizeof(DevState), s) ||
+        cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s) || cudaMemsetAsync(h->d_bits, 0, 4 * size_t((n + 31) / 32 + 8), s) ||
+        cudaMemsetAsync(h->d_rp + n + 1, 0, 4 * 8, s) || cudaMemsetAsync(h->d_ci + h->nnz, 0, 4 * 8, s)) {
         lms::set_error_detail(std::string("upload: ") + cudaGetErrorString(cudaGetLastError()));
         return fail(LMS_ERR_CUDA);
     }
@@ -527,6 +622,16 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
         lms::set_error_detail(std::string("create: ") + cudaGetErrorString(e));
         return fail(LMS_ERR_CUDA);
     }
+    {
+        int dev = 0;
+        cudaDeviceProp prop;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+            return fail(LMS_ERR_CUDA);
+        h->sms = prop.multiProcessorCount;
+    }
+    if (precision == LMS_FP64) h->tile = 256;
+    h->rp_cur = h->rp;
+    if ((rc = build_items(h))) return fail(rc);
     *out = h;
     return LMS_OK;
 }
@@ -554,7 +659,32 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     h->user_perm = p;
     h->colours_valid = false;
     h->coloured_layout = false;
-    return apply_layout(h, p);
+    LMS_TRY(apply_layout(h, p));
+    return build_items(h);
+}
+
+int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile) {
+    if (!h) return LMS_ERR_ARG;
+    if (kernel == LMS_KERNEL_STAGED) {
+        if ((block != 128 && block != 256) || tile < 32 || tile > 4096 || (tile % 32) != 0) return LMS_ERR_ARG;
+    } else if (kernel == LMS_KERNEL_DIRECT) {
+        if (block != 128 && block != 256) return LMS_ERR_ARG;
+    } else {
+        return LMS_ERR_ARG;
+    }
+    LMS_TRY(finish_stats(h));
+    const int old_tile = h->tile;
+    h->kernel = kernel;
+    h->block = block;
+    if (kernel == LMS_KERNEL_STAGED) h->tile = tile;
+    if (h->tile != old_tile) LMS_TRY(build_items(h));
+    if (kernel == LMS_KERNEL_STAGED &&
+        lms::staged_occupancy(h->precision, false, h->block, h->tile, h->e_cap) <= 0) {
+        lms::set_error_detail("tile does not fit in shared memory");
+        return LMS_ERR_ARG;
+    }
+    h->graphs.clear();
+    return LMS_OK;
 }
 
 int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done) {
@@ -572,11 +702,16 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
 
     if (tol < 0.0) {
         std::string key = "fixed/" + std::to_string(mode) + "/" + std::to_string(max_iters) + "/" + std::to_string(base);
+        key += "/" + std::to_string(h->kernel) + "/" + std::to_string(h->block) + "/" + std::to_string(h->tile);
         cudaGraphExec_t exec;
         int64_t kernels = 0;
+        const int32_t slots = max_iters * launches_per_sweep(h, mode);
+        LMS_TRY(ensure_queue(h, slots));
         LMS_TRY(get_graph(h, key,
                           [&](cudaStream_t cs) -> int {
+                              h->slot_next = 0;
                               LMS_CUDA(cudaMemsetAsync(h->d_state, 0, sizeof(DevState), cs));
+                              LMS_CUDA(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t) * slots, cs));
                               for (int32_t k = 1; k <= max_iters; ++k)
                                   LMS_TRY(issue_sweep(h, mode, base, k, k == max_iters, false, cs));
                               return LMS_OK;
@@ -609,11 +744,16 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
     char tol_hex[64];
     std::snprintf(tol_hex, sizeof(tol_hex), "%a", tol);
     std::string key = "stop/" + std::to_string(mode) + "/" + std::to_string(base) + "/" + std::to_string(max_iters) +
-                      "/" + tol_hex;
+                      "/" + tol_hex + "/" + std::to_string(h->kernel) + "/" + std::to_string(h->block) + "/" +
+                      std::to_string(h->tile);
     cudaGraphExec_t exec;
     int64_t kernels = 0;
+    const int32_t slots = kChunk * launches_per_sweep(h, mode);
+    LMS_TRY(ensure_queue(h, slots));
     LMS_TRY(get_graph(h, key,
                       [&](cudaStream_t cs) -> int {
+                          h->slot_next = 0;
+                          LMS_CUDA(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t) * slots, cs));
                           for (int32_t i = 0; i < kChunk; ++i) {
                               const int k1 = 1 + i;  // chunks start at odd sweep indices (kChunk is even)
                               LMS_TRY(issue_sweep(h, mode, base, k1, true, true, cs));
@@ -783,10 +923,22 @@ struct lms_batch_s {
     int64_t n_total = 0, n_int = 0, nnz_total = 0;
     std::vector<int64_t> voff;          // vertex offset of each mesh (k+1)
     std::vector<int32_t> perm;          // global new_to_old
+    std::vector<int32_t> rp;            // relabelled global row offsets (host copy, for the tile table)
     std::vector<double> cs;             // per mesh (cx, cy, inv_s, s)
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_perm = nullptr, *d_item_mesh = nullptr, *d_queue = nullptr;
+    int32_t* d_err = nullptr;           // set by a kernel whose bounded wait expired
     uint32_t* d_bits = nullptr;
     int2* d_items = nullptr;
+    int4* d_items4 = nullptr;           // (first vertex, end vertex, first entry, end entry)
+    int32_t e_cap = 0;                  // max CSR entries of a tile
+    // SELL-C-sigma work layout (built on demand for the current tile size)
+    int32_t* d_sell_col = nullptr;
+    int2* d_sell_slice = nullptr;
+    int32_t* d_sell_slot = nullptr;
+    int2* d_sell_items = nullptr;
+    int64_t sell_col_cap = 0, sell_slice_cap = 0, sell_items_cap = 0;
+    int32_t sell_n_items = 0;
+    int sell_sigma = 0;                 // tile size the SELL tables were built for (0 = none)
     float2* d_xy[3] = {nullptr, nullptr, nullptr};  // ping-pong + autotune scratch
     double* d_xy64 = nullptr;           // FP64 staging, original order
     double* d_fixed = nullptr;          // caller's last coordinates, original order (boundary values)
@@ -794,7 +946,7 @@ struct lms_batch_s {
     int cur = 0;
     int32_t queue_slots = 0;
     // launch configuration
-    int block = 256, lanes = 1, tile = 1024, ctas_per_sm = 0;
+    int kernel = LMS_KERNEL_DIRECT, block = 128, lanes = 1, tile = 512, ctas_per_sm = 0, halo = 0;
     bool configured = false;
     int32_t n_items = 0;
     int items_tile = 0;                 // tile size the item table was built for
@@ -818,20 +970,115 @@ namespace {
 int batch_build_items(lms_batch_s* b, int tile) {
     if (b->items_tile == tile) return LMS_OK;
     std::vector<int2> items;
+    std::vector<int4> items4;
     std::vector<int32_t> im;
+    int32_t e_cap = 0;
     for (int32_t m = 0; m < b->k; ++m)
         for (int64_t v = b->voff[m]; v < b->voff[m + 1]; v += tile) {
-            items.push_back(make_int2(int32_t(v), int32_t(std::min<int64_t>(v + tile, b->voff[m + 1]))));
+            const int32_t va = int32_t(v), vb = int32_t(std::min<int64_t>(v + tile, b->voff[m + 1]));
+            items.push_back(make_int2(va, vb));
+            items4.push_back(make_int4(va, vb, b->rp[va], b->rp[vb]));
+            e_cap = std::max(e_cap, b->rp[vb] - b->rp[va]);
             im.push_back(m);
         }
     if (int64_t(items.size()) > b->items_capacity) return LMS_ERR_STATE;
     LMS_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaMemcpyAsync(b->d_items4, items4.data(), sizeof(int4) * items4.size(), cudaMemcpyHostToDevice,
+                             b->stream));
     LMS_CUDA(cudaMemcpyAsync(b->d_item_mesh, im.data(), sizeof(int32_t) * im.size(), cudaMemcpyHostToDevice, b->stream));
     LMS_CUDA(cudaStreamSynchronize(b->stream));
     b->n_items = int32_t(items.size());
     b->items_tile = tile;
+    b->e_cap = e_cap;
     b->graphs.clear();
     return LMS_OK;
+}
+
+// SELL-C-sigma tables for sorting windows of `sigma` vertices (the tiles).  Reads the relabelled CSR and
+// boundary bits back from the device.
+int batch_build_sell(lms_batch_s* b, int sigma) {
+    if (b->sell_sigma == sigma) return LMS_OK;
+    const int32_t N = int32_t(b->n_total);
+    const int64_t E = b->nnz_total;
+    std::vector<int32_t> ci(std::max<int64_t>(1, E));
+    std::vector<uint32_t> bits((N + 31) / 32);
+    LMS_CUDA(cudaMemcpyAsync(ci.data(), b->d_ci, 4 * size_t(E), cudaMemcpyDeviceToHost, b->stream));
+    LMS_CUDA(cudaMemcpyAsync(bits.data(), b->d_bits, 4 * bits.size(), cudaMemcpyDeviceToHost, b->stream));
+    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    const std::vector<int32_t>& rp = b->rp;
+    std::vector<int32_t> col;
+    std::vector<int2> slices, items;
+    std::vector<int32_t> slots;
+    col.reserve(size_t(E * 1.1) + 64);
+    std::vector<std::pair<int32_t, int32_t>> verts;  // (-degree, position): stable by position
+    for (int32_t m = 0; m < b->k; ++m)
+        for (int64_t t0 = b->voff[m]; t0 < b->voff[m + 1]; t0 += sigma) {
+            const int64_t t1 = std::min<int64_t>(t0 + sigma, b->voff[m + 1]);
+            verts.clear();
+            for (int64_t v = t0; v < t1; ++v)
+                if (!((bits[v >> 5] >> (v & 31)) & 1u)) verts.push_back({-(rp[v + 1] - rp[v]), int32_t(v)});
+            if (verts.empty()) continue;
+            std::stable_sort(verts.begin(), verts.end());
+            const int32_t first_slice = int32_t(slices.size());
+            for (size_t s0 = 0; s0 < verts.size(); s0 += 32) {
+                const size_t s1 = std::min(verts.size(), s0 + 32);
+                const int32_t deg = -verts[s0].first;  // largest in the slice
+                const int64_t base = int64_t(col.size());
+                if (base + 32 * int64_t(deg) >= INT32_MAX) return LMS_ERR_ARG;
+                slices.push_back(make_int2(int32_t(base), deg));
+                col.resize(col.size() + 32 * size_t(deg), -1);
+                for (size_t l = 0; l < 32; ++l) {
+                    if (s0 + l < s1) {
+                        const int32_t v = verts[s0 + l].second;
+                        slots.push_back(v);
+                        for (int32_t j = 0; j < rp[v + 1] - rp[v]; ++j) col[base + 32 * j + l] = ci[rp[v] + j];
+                    } else {
+                        slots.push_back(-1);
+                    }
+                }
+            }
+            items.push_back(make_int2(first_slice, int32_t(slices.size())));
+        }
+    if (int64_t(col.size()) > b->sell_col_cap) {
+        LMS_TRY(b->arena.get(&b->d_sell_col, col.size() + 64));
+        b->sell_col_cap = int64_t(col.size()) + 64;
+    }
+    if (int64_t(slices.size()) > b->sell_slice_cap) {
+        LMS_TRY(b->arena.get(&b->d_sell_slice, slices.size() + 16));
+        LMS_TRY(b->arena.get(&b->d_sell_slot, 32 * (slices.size() + 16)));
+        b->sell_slice_cap = int64_t(slices.size()) + 16;
+    }
+    if (int64_t(items.size()) > b->sell_items_cap) {
+        LMS_TRY(b->arena.get(&b->d_sell_items, items.size() + 16));
+        b->sell_items_cap = int64_t(items.size()) + 16;
+    }
+    LMS_CUDA(cudaMemcpyAsync(b->d_sell_col, col.data(), 4 * col.size(), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaMemcpyAsync(b->d_sell_slice, slices.data(), sizeof(int2) * slices.size(), cudaMemcpyHostToDevice,
+                             b->stream));
+    LMS_CUDA(cudaMemcpyAsync(b->d_sell_slot, slots.data(), 4 * slots.size(), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaMemcpyAsync(b->d_sell_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                             b->stream));
+    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    b->sell_n_items = int32_t(items.size());
+    b->sell_sigma = sigma;
+    b->graphs.clear();
+    return LMS_OK;
+}
+
+lms::StagedArgs batch_staged_args(lms_batch_s* b, int src, int dst, int slot) {
+    lms::StagedArgs a{};
+    a.row_ptr = b->d_rp;
+    a.col_idx = b->d_ci;
+    a.bnd_bits = b->d_bits;
+    a.src = b->d_xy[src];
+    a.dst = b->d_xy[dst];
+    a.items = b->d_items4;
+    a.n_items = b->n_items;
+    a.queue = b->d_queue + slot;
+    a.tile_cap = b->items_tile;
+    a.e_cap = b->e_cap;
+    a.err = b->d_err;
+    return a;
 }
 
 SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
@@ -844,11 +1091,42 @@ SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
     a.items = b->d_items;
     a.n_items = b->n_items;
     a.queue = b->d_queue + slot;
+    a.v_end = int32_t(b->n_total);
+    a.win_halo = b->halo;
     return a;
 }
 
+int batch_occupancy(lms_batch_s* b) {
+    if (b->kernel == LMS_KERNEL_SELL) return lms::batch_sell_occupancy(b->block, b->lanes);
+    if (b->kernel == LMS_KERNEL_STAGED)
+        return lms::staged_occupancy(LMS_FP32, false, b->block, b->items_tile, b->e_cap);
+    return lms::batch_sweep_occupancy(b->block, b->lanes, b->items_tile, b->halo);
+}
+
+// one sweep of the batch on stream s: reads buffer src, writes dst, counts tiles in queue slot `slot`
+int batch_issue(lms_batch_s* b, int src, int dst, int slot, int grid, cudaStream_t s) {
+    if (b->kernel == LMS_KERNEL_SELL) {
+        lms::SellArgs a{};
+        a.col = b->d_sell_col;
+        a.slice = b->d_sell_slice;
+        a.slot = b->d_sell_slot;
+        a.src = b->d_xy[src];
+        a.dst = b->d_xy[dst];
+        a.items = b->d_sell_items;
+        a.n_items = b->sell_n_items;
+        a.queue = b->d_queue + slot;
+        return check_launch(lms::launch_batch_sell(a, b->block, b->lanes, grid, s), "sell_sweep");
+    }
+    if (b->kernel == LMS_KERNEL_STAGED)
+        return check_launch(lms::launch_sweep_staged(LMS_FP32, false, batch_staged_args(b, src, dst, slot), grid,
+                                                     b->block, s),
+                            "staged_sweep");
+    return check_launch(lms::launch_batch_sweep(batch_args(b, src, dst, slot), b->block, b->lanes, grid, b->items_tile, s),
+                        "batch_sweep");
+}
+
 int batch_grid(lms_batch_s* b) {
-    int occ = lms::batch_sweep_occupancy(b->block, b->lanes);
+    int occ = batch_occupancy(b);
     if (occ <= 0) occ = 1;
     int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
     return std::max(1, per_sm * b->sms);
@@ -877,7 +1155,7 @@ std::string autotune_key(lms_batch_s* b) {
         return l;
     };
     std::ostringstream os;
-    os << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    os << "v5|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
     std::string s = os.str();
     for (auto& c : s)
         if (c == ' ') c = '_';
@@ -985,8 +1263,9 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     for (int32_t m = 0; m < k; ++m) max_items += (meshes[m].n + 127) / 128;
     b->items_capacity = max_items;
     int rc = LMS_OK;
-    if ((rc = A.get(&b->d_rp, N + 1)) || (rc = A.get(&b->d_ci, std::max(1, E))) || (rc = A.get(&b->d_perm, N)) ||
-        (rc = A.get(&b->d_bits, (N + 31) / 32 + 4)) || (rc = A.get(&b->d_xy[0], N)) || (rc = A.get(&b->d_xy[1], N)) ||
+    if ((rc = A.get(&b->d_rp, N + 1 + 8)) || (rc = A.get(&b->d_ci, E + 8)) || (rc = A.get(&b->d_perm, N)) ||
+        (rc = A.get(&b->d_bits, (N + 31) / 32 + 8)) || (rc = A.get(&b->d_err, 2)) ||
+        (rc = A.get(&b->d_items4, max_items)) || (rc = A.get(&b->d_xy[0], N)) || (rc = A.get(&b->d_xy[1], N)) ||
         (rc = A.get(&b->d_xy[2], N)) || (rc = A.get(&b->d_xy64, 2 * size_t(N))) || (rc = A.get(&b->d_fixed, 2 * size_t(N))) ||
         (rc = A.get(&b->d_cs, 4 * size_t(k))) ||
         (rc = A.get(&b->d_items, max_items)) || (rc = A.get(&b->d_item_mesh, max_items)) ||
@@ -994,7 +1273,9 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         (rc = orig.get(&d_inv, N)) || (rc = orig.get(&d_bnd0, N)))
         return fail_orig(rc);
     cudaStream_t s = b->stream;
-    if (cudaMemcpyAsync(d_rp0, rp0.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s) ||
+    if (cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int32_t), s) || cudaMemsetAsync(b->d_bits, 0, 4 * ((N + 31) / 32 + 8), s) ||
+        cudaMemsetAsync(b->d_rp, 0, 4 * size_t(N + 1 + 8), s) || cudaMemsetAsync(b->d_ci, 0, 4 * size_t(E + 8), s) ||
+        cudaMemcpyAsync(d_rp0, rp0.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(d_ci0, ci0.data(), 4 * size_t(E), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(d_bnd0, bnd0.data(), size_t(N), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(b->d_xy64, xy0.data(), 16 * size_t(N), cudaMemcpyHostToDevice, s) ||
@@ -1056,9 +1337,10 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     for (int r : status)
         if (r != LMS_OK) return fail_orig(r);
     // relabel on the device
-    std::vector<int32_t> inv(N), rp(N + 1);
+    std::vector<int32_t> inv(N);
+    std::vector<int32_t>& rp = b->rp;
+    rp.assign(N + 1, 0);
     for (int32_t i = 0; i < N; ++i) inv[b->perm[i]] = i;
-    rp[0] = 0;
     for (int32_t i = 0; i < N; ++i) rp[i + 1] = rp[i] + (rp0[b->perm[i] + 1] - rp0[b->perm[i]]);
     cudaError_t e = cudaMemcpyAsync(b->d_perm, b->perm.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(d_inv, inv.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
@@ -1071,41 +1353,56 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         return fail_orig(LMS_ERR_CUDA);
     }
     orig.release_all();
-    if ((rc = batch_build_items(b, 1024))) return fail(rc);
-    for (int i = 0; i < 2; ++i) {
-        e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy64, b->d_xy[i],
-                                      b->d_cs, s);
-        if (e) return fail(check_launch(e, "batch_load_xy"));
-    }
+    if ((rc = batch_build_items(b, b->tile))) return fail(rc);
+    e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_fixed, b->d_xy[0],
+                                  b->d_xy[1], b->d_cs, b->d_err + 1, s);
+    if (e) return fail(check_launch(e, "batch_load_xy"));
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LMS_ERR_CUDA);
     *out = b;
     return LMS_OK;
 }
 
-int lms_batch_get_config(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm) {
+int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile,
+                         int32_t* halo, int32_t* ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
+    if (kernel) *kernel = b->kernel;
+    if (halo) *halo = b->halo;
     if (block) *block = b->block;
     if (lanes) *lanes = b->lanes;
     if (tile) *tile = b->tile;
-    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : lms::batch_sweep_occupancy(b->block, b->lanes);
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, batch_occupancy(b)) : batch_occupancy(b);
     return LMS_OK;
 }
 
-int lms_batch_set_config(lms_batch b, int32_t block, int32_t lanes, int32_t tile, int32_t ctas_per_sm) {
+int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t lanes, int32_t tile, int32_t halo,
+                         int32_t ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
-    if ((block != 128 && block != 256 && block != 512) || (lanes != 1 && lanes != 2 && lanes != 4) || tile < 128 ||
-        tile > 65536 || (tile % 128) != 0 || ctas_per_sm < 0)
+    if ((kernel != LMS_KERNEL_DIRECT && kernel != LMS_KERNEL_STAGED && kernel != LMS_KERNEL_SELL) ||
+        (block != 128 && block != 256 && block != 512) ||
+        (lanes != 1 && lanes != 2 && lanes != 4 && lanes != -4 && lanes != -8) || tile < 128 || tile > 65536 ||
+        (tile % 128) != 0 || ctas_per_sm < 0 || halo < 0 || halo > 8192 || (lanes > 1 && halo != 0))
         return LMS_ERR_ARG;
+    if (kernel == LMS_KERNEL_STAGED && (block > 256 || lanes != 1 || tile > 4096 || halo != 0)) return LMS_ERR_ARG;
+    if (kernel == LMS_KERNEL_SELL && ((lanes != 1 && lanes != -4 && lanes != -8) || halo != 0)) return LMS_ERR_ARG;
+    b->halo = halo;
+    b->kernel = kernel;
     b->block = block;
     b->lanes = lanes;
     b->tile = tile;
     b->ctas_per_sm = ctas_per_sm;
     b->configured = true;
     b->graphs.clear();
-    return batch_build_items(b, tile);
+    LMS_TRY(batch_build_items(b, tile));
+    if (kernel == LMS_KERNEL_SELL) LMS_TRY(batch_build_sell(b, tile));
+    if (batch_occupancy(b) <= 0) {
+        lms::set_error_detail("launch configuration does not fit on the device");
+        return LMS_ERR_ARG;
+    }
+    return LMS_OK;
 }
 
-int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* ctas_per_sm) {
+int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* halo,
+                       int32_t* ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
     const char* cache = std::getenv("LMS_AUTOTUNE_CACHE");
     const std::string key = autotune_key(b);
@@ -1115,65 +1412,77 @@ int lms_batch_autotune(lms_batch b, int32_t* block, int32_t* lanes, int32_t* til
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string kk;
-            int bl, la, ti, cp;
-            if ((is >> kk >> bl >> la >> ti >> cp) && kk == key &&
-                lms_batch_set_config(b, bl, la, ti, cp) == LMS_OK) {
-                return lms_batch_get_config(b, block, lanes, tile, ctas_per_sm);
+            int kn, bl, la, ti, ha, cp;
+            if ((is >> kk >> kn >> bl >> la >> ti >> ha >> cp) && kk == key &&
+                lms_batch_set_config(b, kn, bl, la, ti, ha, cp) == LMS_OK) {
+                return lms_batch_get_config(b, kernel, block, lanes, tile, halo, ctas_per_sm);
             }
         }
     }
+    struct Cand {
+        int kernel, block, lanes, tile, halo;
+    };
+    std::vector<Cand> cands;
+    for (int blk : {128, 256})
+        for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti, 0});
+    for (int ti : {256, 512, 1024, 2048})  // sigma outermost: the SELL tables are rebuilt once per sigma
+        for (int blk : {128, 256, 512})
+            for (int ln : {1, -4, -8}) cands.push_back({LMS_KERNEL_SELL, blk, ln, ti, 0});
+    for (int blk : {128, 256, 512})
+        for (int ln : {1, 2, 4, -4, -8})
+            for (int ti : {256, 512, 1024, 2048})
+                for (int ha : {0, 32, 128})
+                    if (ti >= blk / std::max(ln, 1) && (ln <= 1 || ha == 0))
+                        cands.push_back({LMS_KERNEL_DIRECT, blk, ln, ti, ha});
     cudaStream_t s = b->stream;
     cudaEvent_t e0, e1;
     LMS_CUDA(cudaEventCreate(&e0));
     LMS_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bb = 256, bl = 1, bt = 1024, bc = 0;
-    const int reps = 5;
+    Cand win = cands.front();
+    const int reps = 20, rounds = 2;
+    const bool verbose = std::getenv("LMS_AUTOTUNE_VERBOSE") != nullptr;
     LMS_TRY(ensure_queue(b, reps + 2));
-    for (int blk : {128, 256, 512})
-        for (int ln : {1, 2, 4})
-            for (int ti : {256, 512, 1024, 2048, 4096}) {
-                if (ti < blk / ln) continue;
-                b->block = blk;
-                b->lanes = ln;
-                b->ctas_per_sm = 0;
-                LMS_TRY(batch_build_items(b, ti));
-                const int grid = batch_grid(b);
-                // reads buffer cur, writes the scratch buffer: the batch's positions are untouched
-                LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * (reps + 1), s));
-                SweepArgs a = batch_args(b, b->cur, 2, reps);
-                LMS_TRY(check_launch(lms::launch_batch_sweep(a, blk, ln, grid, s), "autotune"));
-                LMS_CUDA(cudaEventRecord(e0, s));
-                for (int r = 0; r < reps; ++r) {
-                    a = batch_args(b, b->cur, 2, r);
-                    LMS_TRY(check_launch(lms::launch_batch_sweep(a, blk, ln, grid, s), "autotune"));
-                }
-                LMS_CUDA(cudaEventRecord(e1, s));
-                LMS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                LMS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    bb = blk;
-                    bl = ln;
-                    bt = ti;
-                    bc = 0;
-                }
-            }
+    for (const Cand& c : cands) {
+        if (lms_batch_set_config(b, c.kernel, c.block, c.lanes, c.tile, c.halo, 0) != LMS_OK) continue;
+        const int grid = batch_grid(b);
+        // reads buffer cur, writes the scratch buffer: the batch's positions are untouched
+        LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * (reps + 1), s));
+        LMS_TRY(batch_issue(b, b->cur, 2, reps, grid, s));
+        float ms = 1e30f;
+        for (int round = 0; round < rounds; ++round) {
+            LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * reps, s));
+            LMS_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) LMS_TRY(batch_issue(b, b->cur, 2, r, grid, s));
+            LMS_CUDA(cudaEventRecord(e1, s));
+            LMS_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            LMS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
+        }
+        if (verbose)
+            std::fprintf(stderr, "[lms autotune] kernel=%d block=%d lanes=%d tile=%d halo=%d grid=%d e_cap=%d: %.4f ms/sweep\n",
+                         c.kernel, c.block, c.lanes, c.tile, c.halo, grid, b->e_cap, ms / reps);
+        if (ms < best) {
+            best = ms;
+            win = c;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    LMS_TRY(lms_batch_set_config(b, bb, bl, bt, bc));
+    LMS_TRY(lms_batch_set_config(b, win.kernel, win.block, win.lanes, win.tile, win.halo, 0));
     if (cache) {
         std::ofstream f(cache, std::ios::app);
-        f << key << " " << bb << " " << bl << " " << bt << " " << bc << "\n";
+        f << key << " " << win.kernel << " " << win.block << " " << win.lanes << " " << win.tile << " " << win.halo
+          << " 0\n";
     }
-    return lms_batch_get_config(b, block, lanes, tile, ctas_per_sm);
+    return lms_batch_get_config(b, kernel, block, lanes, tile, halo, ctas_per_sm);
 }
 
 int lms_batch_smooth(lms_batch b, int32_t iters) {
     if (!b || iters < 0) return LMS_ERR_ARG;
     if (iters == 0) return LMS_OK;
-    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr));
+    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
     LMS_TRY(ensure_queue(b, iters));
     const int base = b->cur;
     std::string key = std::to_string(iters) + "/" + std::to_string(base);
@@ -1191,8 +1500,7 @@ int lms_batch_smooth(lms_batch b, int32_t iters) {
                 LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * iters, cs));
                 for (int32_t i = 0; i < iters; ++i) {
                     const int src = (base + i) & 1;
-                    SweepArgs a = batch_args(b, src, src ^ 1, i);
-                    LMS_TRY(check_launch(lms::launch_batch_sweep(a, b->block, b->lanes, grid, cs), "batch_sweep"));
+                    LMS_TRY(batch_issue(b, src, src ^ 1, i, grid, cs));
                 }
                 return LMS_OK;
             },
@@ -1206,6 +1514,21 @@ int lms_batch_smooth(lms_batch b, int32_t iters) {
     return LMS_OK;
 }
 
+int batch_check_err(lms_batch_s* b) {
+    int32_t err[2] = {0, 0};
+    LMS_CUDA(cudaMemcpyAsync(err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost, b->stream));
+    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    if (err[0]) {
+        lms::set_error_detail("a bounded wait on a tile copy expired");
+        return LMS_ERR_TIMEOUT;
+    }
+    if (err[1]) {
+        lms::set_error_detail("the last coordinates passed in contain a value that is not finite");
+        return LMS_ERR_ARG;
+    }
+    return LMS_OK;
+}
+
 int lms_batch_get_all_coords(lms_batch b, double* xy) {
     if (!b || !xy) return LMS_ERR_ARG;
     cudaStream_t s = b->stream;
@@ -1214,7 +1537,7 @@ int lms_batch_get_all_coords(lms_batch b, double* xy) {
                          "batch_store_xy"));
     LMS_CUDA(cudaMemcpyAsync(xy, b->d_xy64, 16 * size_t(b->n_total), cudaMemcpyDeviceToHost, s));
     LMS_CUDA(cudaStreamSynchronize(s));
-    return LMS_OK;
+    return batch_check_err(b);
 }
 
 int lms_batch_get_coords(lms_batch b, int32_t mesh, double* xy) {
@@ -1226,19 +1549,19 @@ int lms_batch_get_coords(lms_batch b, int32_t mesh, double* xy) {
     const int64_t v0 = b->voff[mesh], nv = b->voff[mesh + 1] - v0;
     LMS_CUDA(cudaMemcpyAsync(xy, b->d_xy64 + 2 * v0, 16 * size_t(nv), cudaMemcpyDeviceToHost, s));
     LMS_CUDA(cudaStreamSynchronize(s));
-    return LMS_OK;
+    return batch_check_err(b);
 }
 
 int lms_batch_set_all_coords(lms_batch b, const double* xy) {
     if (!b || !xy) return LMS_ERR_ARG;
-    if (!all_finite(xy, 2 * b->n_total)) return LMS_ERR_ARG;
     cudaStream_t s = b->stream;
-    LMS_CUDA(cudaMemcpyAsync(b->d_xy64, xy, 16 * size_t(b->n_total), cudaMemcpyHostToDevice, s));
-    LMS_CUDA(cudaMemcpyAsync(b->d_fixed, b->d_xy64, 16 * size_t(b->n_total), cudaMemcpyDeviceToDevice, s));
-    for (int i = 0; i < 2; ++i)
-        LMS_TRY(check_launch(lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_xy64,
-                                                       b->d_xy[i], b->d_cs, s),
-                             "batch_load_xy"));
+    // the input lands in d_fixed (it also serves the boundary values on output); finiteness is checked
+    // by the load kernel and reported by the next call that returns host data
+    LMS_CUDA(cudaMemsetAsync(b->d_err + 1, 0, sizeof(int32_t), s));
+    LMS_CUDA(cudaMemcpyAsync(b->d_fixed, xy, 16 * size_t(b->n_total), cudaMemcpyHostToDevice, s));
+    LMS_TRY(check_launch(lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_fixed,
+                                                   b->d_xy[0], b->d_xy[1], b->d_cs, b->d_err + 1, s),
+                         "batch_load_xy"));
     b->cur = 0;
     return LMS_OK;
 }

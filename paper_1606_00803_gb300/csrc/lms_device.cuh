@@ -1,0 +1,53 @@
+// lms_device.cuh - device helpers shared by the sweep kernels (lms_kernels.cu, lms_staged.cu).
+#pragma once
+
+#include <cstdint>
+
+#include "lms_internal.h"
+
+namespace lms {
+namespace dev {
+
+__device__ __forceinline__ bool boundary_bit(const uint32_t* __restrict__ bits, int32_t v) {
+    return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// s / d for a positive integer d, correctly rounded: y = RN(1/d) from the table, q = RN(s*y), then one
+// correction q + RN(s - d*q)*y with fused operations (Markstein's division refinement, IBM J. Res. Dev.
+// 34(1), 1990).  About three FP64 operations instead of a full IEEE division; lms_selftest_div64 checks it
+// against IEEE division.
+__device__ __forceinline__ double div_by_count(double s, int32_t d, const double* recip) {
+    if (d <= kMaxRecipDeg) {
+        const double y = recip[d];
+        const double q = __dmul_rn(s, y);
+        const double r = __fma_rn(-q, static_cast<double>(d), s);
+        return __fma_rn(r, y, q);
+    }
+    return __ddiv_rn(s, static_cast<double>(d));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void record_disp(unsigned long long* disp2, double d2) {
+    // non-negative doubles order like their bit patterns
+    unsigned long long m = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(d2)));
+    if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(disp2, m);
+}
+
+
+}  // namespace dev
+}  // namespace lms

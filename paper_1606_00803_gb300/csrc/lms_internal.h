@@ -60,12 +60,52 @@ struct SweepArgs {
     const DevState* state;         // stop flag (NULL: never stop)
     unsigned long long* disp2;     // max squared displacement accumulator (NULL: off)
     const double* recip;           // [kMaxRecipDeg+1] RN(1/d) for the FP64 exact division
+    int32_t win_halo;              // batched: positions of [tile - halo, tile + halo) staged in shared memory
 };
+
+// Tile-staged sweep (lms_staged.cu): items[i] = (first vertex, end vertex, first CSR entry, end entry)
+// of a tile; tiles never cross a mesh or a colour range.  row_ptr, col_idx and bnd_bits must have at
+// least 8 readable padding entries past their ends (copies are rounded to 16 bytes).
+struct StagedArgs {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const uint32_t* bnd_bits;      // NULL: every vertex of every tile is interior
+    const void* src;
+    void* dst;
+    const int4* items;
+    int32_t n_items;
+    int32_t* queue;                // tile counter of this launch (zeroed before it)
+    int32_t tile_cap;              // max vertices per tile
+    int32_t e_cap;                 // max CSR entries per tile
+    const DevState* state;         // stop flag (NULL: never stop)
+    unsigned long long* disp2;     // max squared displacement (NULL: off)
+    const double* recip;           // FP64 reciprocal table
+    int32_t* err;                  // set to 1 when a bounded wait expired
+};
+size_t staged_smem_bytes(int precision, int32_t tile_cap, int32_t e_cap);
+cudaError_t launch_sweep_staged(int precision, bool in_place, const StagedArgs& a, int grid, int block,
+                                cudaStream_t stream);
+int staged_occupancy(int precision, bool in_place, int block, int32_t tile_cap, int32_t e_cap);
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
-cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, cudaStream_t stream);
-int batch_sweep_occupancy(int block, int lanes);  // resident CTAs per SM (0 on error)
+// Batched FP32 sweep over a SELL-C-sigma work layout (see k_batch_sell).
+struct SellArgs {
+    const int32_t* col;            // column-major neighbour ids per slice, -1 past a slot's row
+    const int2* slice;             // per slice: (first entry, slice degree)
+    const int32_t* slot;           // per slot (32 per slice): storage position of the vertex, -1 = empty
+    const void* src;
+    void* dst;
+    const int2* items;             // per tile: [first slice, end slice)
+    int32_t n_items;
+    int32_t* queue;
+};
+cudaError_t launch_batch_sell(const SellArgs& a, int block, int lanes, int grid, cudaStream_t stream);
+int batch_sell_occupancy(int block, int lanes);
+
+// batched direct sweep; `tile` bounds the vertices of a work item (sizes the halo window)
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, int32_t tile, cudaStream_t stream);
+int batch_sweep_occupancy(int block, int lanes, int32_t tile, int32_t halo);  // resident CTAs per SM (0 on error)
 
 cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
                                      cudaStream_t stream);
@@ -101,9 +141,10 @@ cudaError_t launch_store_xy(int precision, int32_t n, const int32_t* new_to_old,
                             double cx, double cy, double s, const uint8_t* bnd_orig, const double* fixed_xy,
                             cudaStream_t stream);
 // batched: per-tile mesh constants (tile t covers items[t], belongs to mesh item_mesh[t])
+// writes both ping-pong buffers; sets *bad to 1 when an input coordinate is not finite
 cudaError_t launch_batch_load_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
-                                 const int32_t* new_to_old, const double* src_orig, float2* dst,
-                                 const double* mesh_cs, cudaStream_t stream);
+                                 const int32_t* new_to_old, const double* src_orig, float2* dst0, float2* dst1,
+                                 const double* mesh_cs, int32_t* bad, cudaStream_t stream);
 cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
                                   const int32_t* new_to_old, const float2* src, double* dst_orig,
                                   const double* mesh_cs, const uint32_t* bnd_bits, const double* fixed_xy,

@@ -23,99 +23,65 @@
 //         reduced in FP64.
 #include <cfloat>
 #include <cstdint>
+#include <type_traits>
 
+#include "lms_device.cuh"
 #include "lms_internal.h"
 
 namespace lms {
 
 namespace {
+using namespace dev;
 
-__device__ __forceinline__ bool boundary_bit(const uint32_t* __restrict__ bits, int32_t v) {
-    return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
-}
-
-// s / d for a positive integer d, correctly rounded (see the file header).
-__device__ __forceinline__ double div_by_count(double s, int32_t d, const double* recip) {
-    if (d <= kMaxRecipDeg) {
-        const double y = recip[d];
-        const double q = __dmul_rn(s, y);
-        const double r = __fma_rn(-q, static_cast<double>(d), s);
-        return __fma_rn(r, y, q);
-    }
-    return __ddiv_rn(s, static_cast<double>(d));
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+// Eq. 1 for one vertex.  FP64 reads the row kChunk entries at a time - all neighbour ids, then all
+// position gathers, then the sums in row order - so a thread keeps kChunk loads in flight while its FP64
+// adds (1/64 of the FP32 rate on GB300) drain; FP32, issue-bound rather than latency-bound, reads one
+// entry at a time.  FP64: sequential sums and the correctly rounded division (bit-identical to the
+// sequential evaluation); FP32: Kahan sums.  Returns the squared displacement when asked.
+template <bool FP64, bool IN_PLACE>
+__device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, const double* recip, bool want_disp) {
+    constexpr int kChunk = FP64 ? 4 : 1;
+    using V = typename std::conditional<FP64, double2, float2>::type;
+    const V* src = static_cast<const V*>(a.src);
+    V* dst = static_cast<V*>(a.dst);
+    const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+    double dx_ = 0.0, dy_ = 0.0;  // FP64 sums
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;  // FP32 Kahan sums
+    for (int32_t e = e0; e < e1; e += kChunk) {
+        int32_t u[kChunk];
+        V p[kChunk];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
+        for (int g = 0; g < kChunk; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+#pragma unroll
+        for (int g = 0; g < kChunk; ++g)
+            if (u[g] >= 0) p[g] = IN_PLACE ? src[u[g]] : __ldg(src + u[g]);
+#pragma unroll
+        for (int g = 0; g < kChunk; ++g)
+            if (u[g] >= 0) {
+                if constexpr (FP64) {
+                    dx_ = __dadd_rn(dx_, p[g].x);
+                    dy_ = __dadd_rn(dy_, p[g].y);
+                } else {
+                    kahan_add(sx, cx, p[g].x);
+                    kahan_add(sy, cy, p[g].y);
+                }
+            }
     }
-    return v;
-}
-
-__device__ __forceinline__ void record_disp(unsigned long long* disp2, double d2) {
-    // non-negative doubles order like their bit patterns
-    unsigned long long m = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(d2)));
-    if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(disp2, m);
-}
-
-// Eq. 1 for one vertex, FP64.  Returns the squared displacement when asked.
-template <bool IN_PLACE>
-__device__ __forceinline__ double smooth_vertex_f64(const SweepArgs& a, int32_t v, const double* recip,
-                                                    bool want_disp) {
-    const double2* src = static_cast<const double2*>(a.src);
-    double2* dst = static_cast<double2*>(a.dst);
-    const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-    double sx = 0.0, sy = 0.0;
-    for (int32_t e = e0; e < e1; ++e) {
-        const int32_t u = __ldg(a.col_idx + e);
-        const double2 p = IN_PLACE ? src[u] : __ldg(src + u);
-        sx = __dadd_rn(sx, p.x);
-        sy = __dadd_rn(sy, p.y);
+    V r;
+    if constexpr (FP64) {
+        r.x = div_by_count(dx_, e1 - e0, recip);
+        r.y = div_by_count(dy_, e1 - e0, recip);
+    } else {
+        const float d = static_cast<float>(e1 - e0);
+        r.x = __fdiv_rn(__fsub_rn(sx, cx), d);
+        r.y = __fdiv_rn(__fsub_rn(sy, cy), d);
     }
-    double2 r;
-    r.x = div_by_count(sx, e1 - e0, recip);
-    r.y = div_by_count(sy, e1 - e0, recip);
     double d2 = 0.0;
     if (want_disp) {
-        const double2 o = src[v];
-        const double dx = __dsub_rn(r.x, o.x), dy = __dsub_rn(r.y, o.y);
-        d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-    }
-    dst[v] = r;
-    return d2;
-}
-
-// Eq. 1 for one vertex, FP32 with compensated sums.
-template <bool IN_PLACE>
-__device__ __forceinline__ double smooth_vertex_f32(const SweepArgs& a, int32_t v, bool want_disp) {
-    const float2* src = static_cast<const float2*>(a.src);
-    float2* dst = static_cast<float2*>(a.dst);
-    const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-    for (int32_t e = e0; e < e1; ++e) {
-        const int32_t u = __ldg(a.col_idx + e);
-        const float2 p = IN_PLACE ? src[u] : __ldg(src + u);
-        kahan_add(sx, cx, p.x);
-        kahan_add(sy, cy, p.y);
-    }
-    const float d = static_cast<float>(e1 - e0);
-    float2 r;
-    r.x = __fdiv_rn(__fsub_rn(sx, cx), d);
-    r.y = __fdiv_rn(__fsub_rn(sy, cy), d);
-    double d2 = 0.0;
-    if (want_disp) {
-        const float2 o = src[v];
-        const double dx = static_cast<double>(__fsub_rn(r.x, o.x)), dy = static_cast<double>(__fsub_rn(r.y, o.y));
-        d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        const V o = src[v];
+        const double ex = static_cast<double>(r.x) - static_cast<double>(o.x);
+        const double ey = static_cast<double>(r.y) - static_cast<double>(o.y);
+        d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
     }
     dst[v] = r;
     return d2;
@@ -136,24 +102,28 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     const bool want = a.disp2 != nullptr;
     double d2 = 0.0;
     if (v < a.v_end && (a.bnd_bits == nullptr || !boundary_bit(a.bnd_bits, v))) {
-        if (FP64)
-            d2 = smooth_vertex_f64<IN_PLACE>(a, v, s_recip, want);
-        else
-            d2 = smooth_vertex_f32<IN_PLACE>(a, v, want);
+        d2 = smooth_vertex<FP64, IN_PLACE>(a, v, s_recip, want);
     }
     if (want) record_disp(a.disp2, d2);
 }
 
-// Batched FP32 Jacobi: a persistent grid pulls vertex tiles from a device counter.  LANES lanes
-// share one vertex: each Kahan-sums every LANES-th neighbour, then the partial sums are merged
-// with shuffles (compensations folded in first).
-template <int LANES>
+// Batched FP32 Jacobi: a persistent grid pulls vertex tiles from a device counter.
+//   LANES > 1: LANES lanes share one vertex; each Kahan-sums every LANES-th neighbour, then the
+//     partial sums are merged with shuffles (compensations folded in first).
+//   CHUNK > 1 (one lane per vertex): a row is read CHUNK entries at a time - all neighbour ids first,
+//     then all CHUNK position gathers, then the Kahan sums in row order - so each thread keeps CHUNK
+//     independent loads in flight instead of one.
+//   halo > 0: the positions of [tile start - halo, tile end + halo) are first loaded into shared
+//     memory with coalesced loads and neighbours inside that window are read from there.
+template <int LANES, int CHUNK>
 __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
+    extern __shared__ float2 win_s[];
     __shared__ int32_t s_item[2];
     const float2* __restrict__ src = static_cast<const float2*>(a.src);
     float2* __restrict__ dst = static_cast<float2*>(a.dst);
     const int group = threadIdx.x / LANES, sub = threadIdx.x % LANES;
     const int groups = blockDim.x / LANES;
+    const int32_t halo = a.win_halo;
     int buf = 0;
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -162,19 +132,55 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
         if (item >= a.n_items) break;
         if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
         const int2 r = __ldg(a.items + item);
+        int32_t wlo = 0, wlen = 0;
+        if (halo > 0) {
+            wlo = max(r.x - halo, 0);
+            wlen = min(r.y + halo, a.v_end) - wlo;
+            for (int32_t k = threadIdx.x; k < wlen; k += blockDim.x) win_s[k] = __ldg(src + wlo + k);
+            __syncthreads();
+        }
+        auto fetch = [&](int32_t u) -> float2 {
+            const uint32_t o = static_cast<uint32_t>(u - wlo);
+            return o < static_cast<uint32_t>(wlen) ? win_s[o] : __ldg(src + u);
+        };
         for (int32_t base = r.x; base < r.y; base += groups) {
             const int32_t v = base + group;
             bool active = v < r.y && !boundary_bit(a.bnd_bits, v);
             int32_t e0 = 0, e1 = 0;
-            if (active) {
+            if (LANES == 1) {
+                // row_ptr[v + 1] is the next lane's row_ptr[v]; lanes past the tile end read
+                // row_ptr[tile end], and the last lane loads its own
+                const int32_t vv = v < r.y ? v : r.y;
+                e0 = __ldg(a.row_ptr + vv);
+                e1 = __shfl_down_sync(0xffffffffu, e0, 1);
+                if ((threadIdx.x & 31) == 31) e1 = v < r.y ? __ldg(a.row_ptr + v + 1) : e0;
+                if (!active) e1 = e0;
+            } else if (active) {
                 e0 = __ldg(a.row_ptr + v);
                 e1 = __ldg(a.row_ptr + v + 1);
             }
             float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-            for (int32_t e = e0 + sub; e < e1; e += LANES) {
-                const float2 p = __ldg(src + __ldg(a.col_idx + e));
-                kahan_add(sx, cx, p.x);
-                kahan_add(sy, cy, p.y);
+            if (CHUNK > 1) {
+                for (int32_t e = e0; e < e1; e += CHUNK) {
+                    int32_t u[CHUNK];
+                    float2 p[CHUNK];
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? fetch(u[g]) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g)
+                        if (u[g] >= 0) {
+                            kahan_add(sx, cx, p[g].x);
+                            kahan_add(sy, cy, p[g].y);
+                        }
+                }
+            } else {
+                for (int32_t e = e0 + sub; e < e1; e += LANES) {
+                    const float2 p = fetch(__ldg(a.col_idx + e));
+                    kahan_add(sx, cx, p.x);
+                    kahan_add(sy, cy, p.y);
+                }
             }
             float tx = __fsub_rn(sx, cx), ty = __fsub_rn(sy, cy);
             if (LANES > 1) {
@@ -199,6 +205,59 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
             if (active && sub == 0) {
                 const float d = static_cast<float>(e1 - e0);
                 dst[v] = make_float2(__fdiv_rn(tx, d), __fdiv_rn(ty, d));
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+// Batched FP32 Jacobi over a SELL-C-sigma work layout (Kreutzer et al., SIAM J. Sci. Comput. 36(5),
+// 2014): inside every tile the interior vertices are sorted by degree into slices of 32, and a slice's
+// neighbour ids are stored column-major (entry j of slot l at base + 32 j + l, -1 past the slot's row),
+// so lane l of a warp handles slot l and each id load of a warp is one coalesced 128-byte access with
+// the same trip count for all lanes.  Positions stay in the ordering's storage layout; entries keep
+// their row order, so the Kahan sums equal the CSR kernels'.  CTAs pull tiles (slice ranges) from a
+// device counter; warps take the tile's slices round-robin.
+template <int CHUNK>
+__global__ void __launch_bounds__(512) k_batch_sell(SellArgs a) {
+    __shared__ int32_t s_item[2];
+    const float2* __restrict__ src = static_cast<const float2*>(a.src);
+    float2* __restrict__ dst = static_cast<float2*>(a.dst);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int buf = 0;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    for (;;) {
+        const int32_t item = s_item[buf];
+        if (item >= a.n_items) break;
+        if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
+        const int2 r = __ldg(a.items + item);
+        for (int32_t sl = r.x + warp; sl < r.y; sl += nwarps) {
+            const int2 sd = __ldg(a.slice + sl);  // (first entry, slice degree)
+            const int32_t v = __ldg(a.slot + 32 * sl + lane);
+            const int32_t* col = a.col + sd.x + lane;
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            int32_t cnt = 0;
+            for (int32_t j = 0; j < sd.y; j += CHUNK) {
+                int32_t u[CHUNK];
+                float2 p[CHUNK];
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g) u[g] = j + g < sd.y ? __ldg(col + 32 * (j + g)) : -1;
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g)
+                    if (u[g] >= 0) p[g] = __ldg(src + u[g]);
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g)
+                    if (u[g] >= 0) {
+                        kahan_add(sx, cx, p[g].x);
+                        kahan_add(sy, cy, p[g].y);
+                        ++cnt;
+                    }
+            }
+            if (v >= 0) {
+                const float d = static_cast<float>(cnt);
+                dst[v] = make_float2(__fdiv_rn(__fsub_rn(sx, cx), d), __fdiv_rn(__fsub_rn(sy, cy), d));
             }
         }
         __syncthreads();
@@ -394,13 +453,23 @@ __global__ void k_store_xy_f32(int32_t n, const int32_t* __restrict__ new_to_old
     dst[o] = (fixed_xy != nullptr && bnd_orig[o]) ? fixed_xy[o] : denormalise(src[k], cx, cy, s);
 }
 
-// one block per tile; mesh_cs[4m..4m+3] = (cx, cy, inv_s, s)
+// one block per tile; mesh_cs[4m..4m+3] = (cx, cy, inv_s, s).  Writes both ping-pong buffers and raises
+// *bad when an input coordinate is not finite.
 __global__ void k_batch_load_xy(const int2* __restrict__ items, const int32_t* __restrict__ item_mesh,
                                 const int32_t* __restrict__ new_to_old, const double2* __restrict__ src,
-                                float2* __restrict__ dst, const double* __restrict__ mesh_cs) {
+                                float2* __restrict__ dst0, float2* __restrict__ dst1,
+                                const double* __restrict__ mesh_cs, int32_t* bad) {
     const int2 r = items[blockIdx.x];
     const double* cs = mesh_cs + 4 * item_mesh[blockIdx.x];
-    for (int32_t k = r.x + threadIdx.x; k < r.y; k += blockDim.x) dst[k] = normalise(src[new_to_old[k]], cs[0], cs[1], cs[2]);
+    bool finite = true;
+    for (int32_t k = r.x + threadIdx.x; k < r.y; k += blockDim.x) {
+        const double2 p = src[new_to_old[k]];
+        finite = finite && isfinite(p.x) && isfinite(p.y);
+        const float2 q = normalise(p, cs[0], cs[1], cs[2]);
+        dst0[k] = q;
+        dst1[k] = q;
+    }
+    if (!finite) atomicExch(bad, 1);
 }
 
 __global__ void k_batch_store_xy(const int2* __restrict__ items, const int32_t* __restrict__ item_mesh,
@@ -443,26 +512,67 @@ cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int b
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, cudaStream_t stream) {
+size_t batch_window_bytes(int32_t tile, int32_t halo) { return halo > 0 ? 8 * size_t(tile + 2 * halo) : 0; }
+
+using BatchKernel = void (*)(SweepArgs);
+
+// lanes 1/2/4 with one entry at a time, or one lane with chunks of 4/8 (lanes = -4 / -8)
+BatchKernel batch_kernel(int lanes) {
     switch (lanes) {
-        case 1: k_batch_sweep<1><<<grid, block, 0, stream>>>(a); break;
-        case 2: k_batch_sweep<2><<<grid, block, 0, stream>>>(a); break;
-        case 4: k_batch_sweep<4><<<grid, block, 0, stream>>>(a); break;
-        default: return cudaErrorInvalidValue;
+        case 1: return k_batch_sweep<1, 1>;
+        case 2: return k_batch_sweep<2, 1>;
+        case 4: return k_batch_sweep<4, 1>;
+        case -4: return k_batch_sweep<1, 4>;
+        case -8: return k_batch_sweep<1, 8>;
+        default: return nullptr;
     }
+}
+
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, int32_t tile, cudaStream_t stream) {
+    const BatchKernel k = batch_kernel(lanes);
+    if (k == nullptr) return cudaErrorInvalidValue;
+    const size_t smem = batch_window_bytes(tile, a.win_halo);
+    if (smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-int batch_sweep_occupancy(int block, int lanes) {
-    int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
+using SellKernel = void (*)(SellArgs);
+
+SellKernel sell_kernel(int lanes) {
     switch (lanes) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<1>, block, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<2>, block, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<4>, block, 0); break;
-        default: break;
+        case 1: return k_batch_sell<1>;
+        case -4: return k_batch_sell<4>;
+        case -8: return k_batch_sell<8>;
+        default: return nullptr;
     }
-    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_batch_sell(const SellArgs& a, int block, int lanes, int grid, cudaStream_t stream) {
+    const SellKernel k = sell_kernel(lanes);
+    if (k == nullptr) return cudaErrorInvalidValue;
+    k<<<grid, block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_sell_occupancy(int block, int lanes) {
+    const SellKernel k = sell_kernel(lanes);
+    int n = 0;
+    if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+int batch_sweep_occupancy(int block, int lanes, int32_t tile, int32_t halo) {
+    const BatchKernel k = batch_kernel(lanes);
+    if (k == nullptr) return 0;
+    const size_t smem = batch_window_bytes(tile, halo);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
@@ -556,11 +666,12 @@ cudaError_t launch_store_xy(int precision, int32_t n, const int32_t* new_to_old,
 }
 
 cudaError_t launch_batch_load_xy(int32_t n_items, const int2* items, const int32_t* item_mesh,
-                                 const int32_t* new_to_old, const double* src_orig, float2* dst,
-                                 const double* mesh_cs, cudaStream_t stream) {
+                                 const int32_t* new_to_old, const double* src_orig, float2* dst0, float2* dst1,
+                                 const double* mesh_cs, int32_t* bad, cudaStream_t stream) {
     if (n_items <= 0) return cudaSuccess;
     k_batch_load_xy<<<n_items, 256, 0, stream>>>(items, item_mesh, new_to_old,
-                                                 reinterpret_cast<const double2*>(src_orig), dst, mesh_cs);
+                                                 reinterpret_cast<const double2*>(src_orig), dst0, dst1, mesh_cs,
+                                                 bad);
     return cudaGetLastError();
 }
 

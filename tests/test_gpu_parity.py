@@ -286,7 +286,15 @@ def small_batch(count=10):
             for i, s in enumerate(sides)]
 
 
-@pytest.mark.parametrize("config", [(256, 1, 256), (512, 2, 1024), (128, 4, 512), (256, 1, 4096)])
+@pytest.mark.parametrize("config", [(lms.KERNEL_STAGED, 256, 1, 256, 0), (lms.KERNEL_STAGED, 128, 1, 512, 0),
+                                    (lms.KERNEL_STAGED, 256, 1, 2048, 0), (lms.KERNEL_STAGED, 128, 1, 128, 0),
+                                    (lms.KERNEL_DIRECT, 256, 1, 256, 0), (lms.KERNEL_DIRECT, 512, 2, 1024, 0),
+                                    (lms.KERNEL_DIRECT, 128, 4, 512, 0), (lms.KERNEL_DIRECT, 256, 1, 4096, 0),
+                                    (lms.KERNEL_DIRECT, 128, 1, 256, 32), (lms.KERNEL_DIRECT, 256, 1, 1024, 512),
+                                    (lms.KERNEL_DIRECT, 512, 1, 2048, 4096), (lms.KERNEL_DIRECT, 128, -4, 512, 0),
+                                    (lms.KERNEL_DIRECT, 256, -8, 256, 32), (lms.KERNEL_DIRECT, 512, -8, 1024, 0),
+                                    (lms.KERNEL_SELL, 128, 1, 256, 0), (lms.KERNEL_SELL, 256, -4, 1024, 0),
+                                    (lms.KERNEL_SELL, 512, -8, 2048, 0), (lms.KERNEL_SELL, 128, -4, 128, 0)])
 def test_batched_fp32_matches_oracle(config):
     meshes = small_batch()
     with lms.Batch(meshes, ordering=lms.RDR) as b:
@@ -305,7 +313,8 @@ def test_batched_autotune_keeps_positions():
     with lms.Batch(meshes, ordering=lms.BFS) as b:
         before = b.all_coords()
         cfg = b.autotune()
-        assert cfg["block"] in (128, 256, 512) and cfg["lanes"] in (1, 2, 4)
+        assert cfg["kernel"] in (lms.KERNEL_DIRECT, lms.KERNEL_STAGED, lms.KERNEL_SELL)
+        assert cfg["block"] in (128, 256, 512) and cfg["lanes"] in (1, 2, 4, -4, -8)
         assert np.array_equal(b.all_coords(), before)
         b.smooth(7)
         b.smooth(8)
@@ -327,3 +336,45 @@ def test_batched_set_coords_round_trip():
         want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 20)
         o = sum(x["n"] for x in meshes[:i])
         assert err(got[o:o + m["n"]], want, m) <= TOL32
+
+
+@pytest.mark.parametrize("launch", [(lms.KERNEL_DIRECT, 128, 0), (lms.KERNEL_STAGED, 128, 64),
+                                    (lms.KERNEL_STAGED, 256, 256), (lms.KERNEL_STAGED, 256, 1024),
+                                    (lms.KERNEL_STAGED, 128, 1024)])
+def test_sweep_kernels_agree_with_oracle(mesh_mid, launch):
+    # every launch configuration gives the oracle's result: FP64 bit-exact, FP32 within tolerance
+    m = mesh_mid
+    kernel, block, tile = launch
+    p = oracle.order(m, oracle.RDR)
+    want_j, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 21)
+    want_g, _, _ = oracle.gs_smooth(m, p, 9)
+    for precision in (lms.FP64, lms.FP32):
+        with lms.Mesh.from_dict(m, precision) as g:
+            g.reorder(lms.RDR)
+            g.set_launch(kernel, block, max(tile, 32))
+            g.smooth(21)
+            got_j = g.coords()
+            g.set_coords(m["xy"])
+            g.smooth(9, mode=lms.COLORED_GS)
+            got_g = g.coords()
+            st = g.last_stats()
+        if precision == lms.FP64:
+            assert np.array_equal(got_j, want_j) and np.array_equal(got_g, want_g)
+        else:
+            assert err(got_j, want_j, m) <= TOL32 and err(got_g, want_g, m) <= TOL32
+        assert st["max_disp"] > 0
+
+
+def test_batched_rejects_non_finite_coordinates_on_next_read():
+    meshes = small_batch(3)
+    with lms.Batch(meshes, ordering=lms.ORI) as b:
+        xy = np.concatenate([m["xy"] for m in meshes])
+        xy[5, 1] = np.inf
+        b.set_all_coords(xy)
+        with pytest.raises(lms.LmsError) as e:
+            b.all_coords()
+        assert e.value.status == -1
+        xy[5, 1] = 0.5
+        b.set_all_coords(xy)
+        b.smooth(3)
+        assert np.isfinite(b.all_coords()).all()
