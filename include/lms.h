@@ -198,6 +198,26 @@ int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, 
 /* Free a handle and its device memory (NULL is ignored). */
 void lms_destroy(lms_handle h);
 
+/*
+ * FP64 Jacobi sweeps that allocate no device memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (code running inside another framework's memory pool or
+ * under a fixed device-memory budget, services that forbid allocations on their steady-state path).
+ * All buffers are the caller's DEVICE pointers: row_ptr [n+1] and col_idx [row_ptr[n]] (CSR, as for
+ * lms_create), is_boundary [n] (nonzero = fixed), xy [2n] interleaved positions (input; receives the
+ * result), xy_tmp [2n] work buffer (needs no initial contents; distinct from xy).  Runs `iters` sweeps of
+ * Eq. 1 on cuda_stream (NULL = legacy default stream), asynchronously; results equal lms_smooth's FP64
+ * Jacobi bit for bit (sequential row-order sums, IEEE division).  The mesh is not validated.
+ * The sweeps' only scratch - one work-queue counter per sweep - is a fixed 4 KB array inside the library
+ * that every GPU loading the library holds until the process exits.  Hence:
+ *   - iters is limited to 1024 per call (LMS_ERR_ARG beyond, with a message);
+ *   - the first call on a device looks up that array's address (and makes the driver load the library's
+ *     device code), so make it once before any stream capture;
+ *   - every call shares the array: calls whose work overlaps on the GPU (other streams, other threads)
+ *     race and give wrong results; serialise them.
+ */
+int lms_jacobi_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                       double* xy, double* xy_tmp, int32_t iters, void* cuda_stream);
+
 /* Text of the last CUDA error seen by this thread (empty if none). [host] */
 const char* lms_last_error_detail(void);
 
