@@ -420,8 +420,8 @@ def run_ours(args, dist):
                 "launch": cfg, "parallelism": "each rank smooths its own batch" if dist.world > 1 else "1 GPU",
                 "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "kernel": ("k_sweep_staged<fp32>" if cfg["kernel"] == lms.KERNEL_STAGED
-                                    else "k_batch_sweep<%d>" % cfg["lanes"]),
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"]}.get(
+                             cfg["kernel"], "k_batch_sweep<%d>" % cfg["chunk"]),
                          "algorithmic_bytes_per_launch": ab, "launch_ms": sweep_ms,
                          "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 7900.0},
             "cpu_baseline": cpu,
@@ -431,22 +431,35 @@ def run_ours(args, dist):
             "clocks": clocks,
         }
         line.update(extras)
-        traffic = load_traffic()
-        if traffic is not None:
-            line["roofline"]["traffic"] = traffic
+        line["roofline"]["traffic"] = load_traffic(line["roofline"]["kernel"], cfg)
         print(json.dumps(line))
     b.close()
 
 
-def load_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it is current."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def kernel_source_digest():
+    """sha256 over the library's device and host sources: any change makes recorded counters stale."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1606_00803_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def load_traffic(kernel, config):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json), when it was
+    captured from these exact sources and launch configuration; None otherwise."""
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        return t.get("k_batch_sweep_dram_bytes_per_launch")
     except Exception:
         return None
+    if t.get("source_digest") != kernel_source_digest() or t.get("kernel") != kernel:
+        return None
+    if any(t.get("config", {}).get(k) != config.get(k) for k in ("kernel", "block", "chunk", "tile")):
+        return None
+    return t.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------------ reference arm

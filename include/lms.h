@@ -52,7 +52,8 @@ extern "C" {
 /* precision of the stored coordinates and of the sweep arithmetic */
 #define LMS_FP64 0 /* double2 coordinates, FP64 sums and division (results equal the FP64 sequential sums) */
 #define LMS_FP32 1 /* float2 coordinates relative to the bounding-box centre, scaled by the larger box
-                      side; compensated (Kahan) FP32 neighbour sums; quality reduced in FP64 */
+                      side; compensated (Kahan) FP32 neighbour sums, mean by the rounded reciprocal of
+                      the count; quality reduced in FP64 */
 
 /* vertex orderings (Section 5.2.1 compares ORI, BFS and RDR; Fig. 1 adds a random one) */
 #define LMS_ORI 0    /* original order: identity permutation */
@@ -69,7 +70,8 @@ extern "C" {
                             (colour, storage position) order */
 
 /* sweep kernels */
-#define LMS_KERNEL_DIRECT 0 /* thread (or 2/4 lanes) per vertex, CSR and positions loaded through L1 */
+#define LMS_KERNEL_DIRECT 0 /* one thread per vertex; CSR and positions loaded through L1; rows read `chunk`
+                               entries at a time (all ids, then all gathers, then the sums) */
 #define LMS_KERNEL_STAGED 1 /* tile CSR brought to shared memory by TMA bulk copies one tile ahead; neighbour
                                positions gathered edge-parallel into shared memory, then summed per vertex */
 #define LMS_KERNEL_SELL 2   /* batched only: SELL-C-sigma work layout - inside every tile the interior vertices
@@ -258,25 +260,20 @@ int lms_batch_set_all_coords(lms_batch b, const double* xy);
 int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles);
 
 /*
- * Launch configuration of the batched sweep: kernel = LMS_KERNEL_* (SELL: tile
- * = sorting window sigma, lanes 1 / -4 / -8, halo 0), block =
- * threads per CTA (128/256/512; staged: 128 or 256), lanes = lanes per vertex
- * (1, 2 or 4), or -4 / -8 for one lane per vertex reading its row 4 / 8
- * entries at a time (all ids, then all gathers, then the sums; staged: 1), tile = vertices per work item (multiple of 128;
- * staged: at most 4096), halo = direct kernel with one lane per vertex: the
- * positions of [tile start - halo, tile end + halo) are staged in shared
- * memory and in-window neighbours read from there (0 = off; lanes > 1 and
- * staged: 0),
- * ctas_per_sm = resident CTAs of the persistent grid (0 = as many as fit).  lms_batch_autotune times the candidates on the batch
- * (without changing its coordinates), keeps the fastest and returns it;
+ * Launch configuration of the batched sweep: kernel = LMS_KERNEL_*, block =
+ * threads per CTA (128/256/512; staged: 128 or 256), chunk = row entries read
+ * per step (direct: 1, 2, 4 or 8; staged: 1; SELL: 1, 4 or 8), tile =
+ * vertices per work item, a multiple of 128 (staged: at most 4096; SELL: the
+ * degree-sorting window sigma), ctas_per_sm = resident CTAs of the persistent
+ * grid (0 = as many as fit).  lms_batch_autotune times the candidates on the
+ * batch (without changing its coordinates), keeps the fastest and returns it;
  * results are cached in the file named by the LMS_AUTOTUNE_CACHE environment
  * variable when it is set.  Any output pointer may be NULL.
  */
-int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile,
-                         int32_t* halo, int32_t* ctas_per_sm);
-int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t lanes, int32_t tile, int32_t halo,
-                         int32_t ctas_per_sm);
-int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* halo,
+int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
+                         int32_t* ctas_per_sm);
+int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chunk, int32_t tile, int32_t ctas_per_sm);
+int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
                        int32_t* ctas_per_sm);
 
 /* Ordering of mesh `mesh` of a batch ([n_mesh] new_to_old, local ids).  LMS_RANDOM uses seed + mesh. */

@@ -85,9 +85,9 @@ _SIGS = {
     "lms_batch_get_all_coords": ([_P, _P], ctypes.c_int),
     "lms_batch_set_all_coords": ([_P, _P], ctypes.c_int),
     "lms_batch_info": ([_P, _PI64, _PI64, _PI64, _PI32], ctypes.c_int),
-    "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
-    "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
-    "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
+    "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
+    "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
     "lms_batch_get_permutation": ([_P, _I32, _P], ctypes.c_int),
     "lms_batch_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_batch_destroy": ([_P], None),
@@ -388,19 +388,19 @@ class Batch:
                                      ctypes.byref(tiles)), "lms_batch_info")
         return dict(n_total=n.value, n_interior=ni.value, nnz_total=nnz.value, tiles=tiles.value)
 
-    _CFG = ("kernel", "block", "lanes", "tile", "halo", "ctas_per_sm")
+    _CFG = ("kernel", "block", "chunk", "tile", "ctas_per_sm")
 
     def config(self):
-        v = [ctypes.c_int32() for _ in range(6)]
+        v = [ctypes.c_int32() for _ in range(5)]
         _check(_lib().lms_batch_get_config(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_get_config")
         return dict(zip(self._CFG, [x.value for x in v]))
 
-    def set_config(self, kernel, block, lanes, tile, halo=0, ctas_per_sm=0):
-        _check(_lib().lms_batch_set_config(self._handle(), kernel, block, lanes, tile, halo, ctas_per_sm),
+    def set_config(self, kernel, block, chunk, tile, ctas_per_sm=0):
+        _check(_lib().lms_batch_set_config(self._handle(), kernel, block, chunk, tile, ctas_per_sm),
                "lms_batch_set_config")
 
     def autotune(self):
-        v = [ctypes.c_int32() for _ in range(6)]
+        v = [ctypes.c_int32() for _ in range(5)]
         _check(_lib().lms_batch_autotune(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_autotune")
         return dict(zip(self._CFG, [x.value for x in v]))
 

@@ -55,7 +55,7 @@ def build(force=False, verbose=False):
         obj = os.path.join(OUT_DIR, src + ".o")
         if src.endswith(".cu"):
             cmd = [nvcc] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                                   "-c", path, "-o", obj] + inc
+                                   "-c", path, "-o", obj] + inc + os.environ.get("LMS_NVCC_FLAGS", "").split()
         elif src.endswith(".cpp"):
             cmd = ["g++"] + host_flags + ["-c", path, "-o", obj] + inc
         else:

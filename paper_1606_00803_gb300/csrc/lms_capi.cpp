@@ -926,6 +926,7 @@ struct lms_batch_s {
     std::vector<int32_t> rp;            // relabelled global row offsets (host copy, for the tile table)
     std::vector<double> cs;             // per mesh (cx, cy, inv_s, s)
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_perm = nullptr, *d_item_mesh = nullptr, *d_queue = nullptr;
+    // d_rp: relabelled row offsets with the boundary flag in bit 31 (row_ptr[v] | boundary(v) << 31)
     int32_t* d_err = nullptr;           // set by a kernel whose bounded wait expired
     uint32_t* d_bits = nullptr;
     int2* d_items = nullptr;
@@ -946,7 +947,7 @@ struct lms_batch_s {
     int cur = 0;
     int32_t queue_slots = 0;
     // launch configuration
-    int kernel = LMS_KERNEL_DIRECT, block = 128, lanes = 1, tile = 512, ctas_per_sm = 0, halo = 0;
+    int kernel = LMS_KERNEL_DIRECT, block = 128, chunk = 4, tile = 512, ctas_per_sm = 0;
     bool configured = false;
     int32_t n_items = 0;
     int items_tile = 0;                 // tile size the item table was built for
@@ -1092,15 +1093,14 @@ SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
     a.n_items = b->n_items;
     a.queue = b->d_queue + slot;
     a.v_end = int32_t(b->n_total);
-    a.win_halo = b->halo;
     return a;
 }
 
 int batch_occupancy(lms_batch_s* b) {
-    if (b->kernel == LMS_KERNEL_SELL) return lms::batch_sell_occupancy(b->block, b->lanes);
+    if (b->kernel == LMS_KERNEL_SELL) return lms::batch_sell_occupancy(b->block, b->chunk);
     if (b->kernel == LMS_KERNEL_STAGED)
         return lms::staged_occupancy(LMS_FP32, false, b->block, b->items_tile, b->e_cap);
-    return lms::batch_sweep_occupancy(b->block, b->lanes, b->items_tile, b->halo);
+    return lms::batch_sweep_occupancy(b->block, b->chunk);
 }
 
 // one sweep of the batch on stream s: reads buffer src, writes dst, counts tiles in queue slot `slot`
@@ -1115,13 +1115,13 @@ int batch_issue(lms_batch_s* b, int src, int dst, int slot, int grid, cudaStream
         a.items = b->d_sell_items;
         a.n_items = b->sell_n_items;
         a.queue = b->d_queue + slot;
-        return check_launch(lms::launch_batch_sell(a, b->block, b->lanes, grid, s), "sell_sweep");
+        return check_launch(lms::launch_batch_sell(a, b->block, b->chunk, grid, s), "sell_sweep");
     }
     if (b->kernel == LMS_KERNEL_STAGED)
         return check_launch(lms::launch_sweep_staged(LMS_FP32, false, batch_staged_args(b, src, dst, slot), grid,
                                                      b->block, s),
                             "staged_sweep");
-    return check_launch(lms::launch_batch_sweep(batch_args(b, src, dst, slot), b->block, b->lanes, grid, b->items_tile, s),
+    return check_launch(lms::launch_batch_sweep(batch_args(b, src, dst, slot), b->block, b->chunk, grid, s),
                         "batch_sweep");
 }
 
@@ -1155,7 +1155,7 @@ std::string autotune_key(lms_batch_s* b) {
         return l;
     };
     std::ostringstream os;
-    os << "v5|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    os << "v9|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
     std::string s = os.str();
     for (auto& c : s)
         if (c == ' ') c = '_';
@@ -1347,6 +1347,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     if (!e) e = cudaMemcpyAsync(b->d_rp, rp.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
     if (!e) e = lms::launch_gather_rows(N, b->d_perm, d_rp0, d_ci0, b->d_rp, b->d_ci, d_inv, s);
     if (!e) e = lms::launch_boundary_bits(N, b->d_perm, d_bnd0, b->d_bits, s);
+    if (!e) e = lms::launch_flag_boundary_rows(N, b->d_bits, b->d_rp, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) {
         lms::set_error_detail(std::string("batch relabel: ") + cudaGetErrorString(e));
@@ -1362,32 +1363,37 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     return LMS_OK;
 }
 
-int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile,
-                         int32_t* halo, int32_t* ctas_per_sm) {
+int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
+                         int32_t* ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
     if (kernel) *kernel = b->kernel;
-    if (halo) *halo = b->halo;
     if (block) *block = b->block;
-    if (lanes) *lanes = b->lanes;
+    if (chunk) *chunk = b->chunk;
     if (tile) *tile = b->tile;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, batch_occupancy(b)) : batch_occupancy(b);
     return LMS_OK;
 }
 
-int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t lanes, int32_t tile, int32_t halo,
-                         int32_t ctas_per_sm) {
+int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chunk, int32_t tile, int32_t ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
-    if ((kernel != LMS_KERNEL_DIRECT && kernel != LMS_KERNEL_STAGED && kernel != LMS_KERNEL_SELL) ||
-        (block != 128 && block != 256 && block != 512) ||
-        (lanes != 1 && lanes != 2 && lanes != 4 && lanes != -4 && lanes != -8) || tile < 128 || tile > 65536 ||
-        (tile % 128) != 0 || ctas_per_sm < 0 || halo < 0 || halo > 8192 || (lanes > 1 && halo != 0))
-        return LMS_ERR_ARG;
-    if (kernel == LMS_KERNEL_STAGED && (block > 256 || lanes != 1 || tile > 4096 || halo != 0)) return LMS_ERR_ARG;
-    if (kernel == LMS_KERNEL_SELL && ((lanes != 1 && lanes != -4 && lanes != -8) || halo != 0)) return LMS_ERR_ARG;
-    b->halo = halo;
+    if (block != 128 && block != 256 && block != 512) return LMS_ERR_ARG;
+    if (tile < 128 || tile > 65536 || (tile % 128) != 0 || ctas_per_sm < 0) return LMS_ERR_ARG;
+    switch (kernel) {
+        case LMS_KERNEL_DIRECT:
+            if (chunk != 1 && chunk != 2 && chunk != 4 && chunk != 8) return LMS_ERR_ARG;
+            break;
+        case LMS_KERNEL_STAGED:
+            if (block > 256 || chunk != 1 || tile > 4096) return LMS_ERR_ARG;
+            break;
+        case LMS_KERNEL_SELL:
+            if (chunk != 1 && chunk != 4 && chunk != 8) return LMS_ERR_ARG;
+            break;
+        default:
+            return LMS_ERR_ARG;
+    }
     b->kernel = kernel;
     b->block = block;
-    b->lanes = lanes;
+    b->chunk = chunk;
     b->tile = tile;
     b->ctas_per_sm = ctas_per_sm;
     b->configured = true;
@@ -1401,7 +1407,7 @@ int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t lan
     return LMS_OK;
 }
 
-int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* lanes, int32_t* tile, int32_t* halo,
+int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
                        int32_t* ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
     const char* cache = std::getenv("LMS_AUTOTUNE_CACHE");
@@ -1412,28 +1418,23 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* la
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string kk;
-            int kn, bl, la, ti, ha, cp;
-            if ((is >> kk >> kn >> bl >> la >> ti >> ha >> cp) && kk == key &&
-                lms_batch_set_config(b, kn, bl, la, ti, ha, cp) == LMS_OK) {
-                return lms_batch_get_config(b, kernel, block, lanes, tile, halo, ctas_per_sm);
-            }
+            int kn, bl, ch, ti, cp;
+            if ((is >> kk >> kn >> bl >> ch >> ti >> cp) && kk == key && lms_batch_set_config(b, kn, bl, ch, ti, cp) == LMS_OK)
+                return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
         }
     }
     struct Cand {
-        int kernel, block, lanes, tile, halo;
+        int kernel, block, chunk, tile;
     };
     std::vector<Cand> cands;
-    for (int blk : {128, 256})
-        for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti, 0});
-    for (int ti : {256, 512, 1024, 2048})  // sigma outermost: the SELL tables are rebuilt once per sigma
-        for (int blk : {128, 256, 512})
-            for (int ln : {1, -4, -8}) cands.push_back({LMS_KERNEL_SELL, blk, ln, ti, 0});
     for (int blk : {128, 256, 512})
-        for (int ln : {1, 2, 4, -4, -8})
-            for (int ti : {256, 512, 1024, 2048})
-                for (int ha : {0, 32, 128})
-                    if (ti >= blk / std::max(ln, 1) && (ln <= 1 || ha == 0))
-                        cands.push_back({LMS_KERNEL_DIRECT, blk, ln, ti, ha});
+        for (int ch : {1, 2, 4, 8})
+            for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_DIRECT, blk, ch, ti});
+    for (int blk : {128, 256})
+        for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti});
+    for (int ti : {512, 1024, 2048})  // sigma outermost: the SELL tables are rebuilt once per sigma
+        for (int blk : {128, 256})
+            for (int ch : {4, 8}) cands.push_back({LMS_KERNEL_SELL, blk, ch, ti});
     cudaStream_t s = b->stream;
     cudaEvent_t e0, e1;
     LMS_CUDA(cudaEventCreate(&e0));
@@ -1444,7 +1445,7 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* la
     const bool verbose = std::getenv("LMS_AUTOTUNE_VERBOSE") != nullptr;
     LMS_TRY(ensure_queue(b, reps + 2));
     for (const Cand& c : cands) {
-        if (lms_batch_set_config(b, c.kernel, c.block, c.lanes, c.tile, c.halo, 0) != LMS_OK) continue;
+        if (lms_batch_set_config(b, c.kernel, c.block, c.chunk, c.tile, 0) != LMS_OK) continue;
         const int grid = batch_grid(b);
         // reads buffer cur, writes the scratch buffer: the batch's positions are untouched
         LMS_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int32_t) * (reps + 1), s));
@@ -1461,8 +1462,8 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* la
             ms = std::min(ms, t);
         }
         if (verbose)
-            std::fprintf(stderr, "[lms autotune] kernel=%d block=%d lanes=%d tile=%d halo=%d grid=%d e_cap=%d: %.4f ms/sweep\n",
-                         c.kernel, c.block, c.lanes, c.tile, c.halo, grid, b->e_cap, ms / reps);
+            std::fprintf(stderr, "[lms autotune] kernel=%d block=%d chunk=%d tile=%d grid=%d: %.4f ms/sweep\n", c.kernel,
+                         c.block, c.chunk, c.tile, grid, ms / reps);
         if (ms < best) {
             best = ms;
             win = c;
@@ -1470,19 +1471,18 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* la
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    LMS_TRY(lms_batch_set_config(b, win.kernel, win.block, win.lanes, win.tile, win.halo, 0));
+    LMS_TRY(lms_batch_set_config(b, win.kernel, win.block, win.chunk, win.tile, 0));
     if (cache) {
         std::ofstream f(cache, std::ios::app);
-        f << key << " " << win.kernel << " " << win.block << " " << win.lanes << " " << win.tile << " " << win.halo
-          << " 0\n";
+        f << key << " " << win.kernel << " " << win.block << " " << win.chunk << " " << win.tile << " 0\n";
     }
-    return lms_batch_get_config(b, kernel, block, lanes, tile, halo, ctas_per_sm);
+    return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
 }
 
 int lms_batch_smooth(lms_batch b, int32_t iters) {
     if (!b || iters < 0) return LMS_ERR_ARG;
     if (iters == 0) return LMS_OK;
-    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr, nullptr));
     LMS_TRY(ensure_queue(b, iters));
     const int base = b->cur;
     std::string key = std::to_string(iters) + "/" + std::to_string(base);

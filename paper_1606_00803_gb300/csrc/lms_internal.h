@@ -60,7 +60,6 @@ struct SweepArgs {
     const DevState* state;         // stop flag (NULL: never stop)
     unsigned long long* disp2;     // max squared displacement accumulator (NULL: off)
     const double* recip;           // [kMaxRecipDeg+1] RN(1/d) for the FP64 exact division
-    int32_t win_halo;              // batched: positions of [tile - halo, tile + halo) staged in shared memory
 };
 
 // Tile-staged sweep (lms_staged.cu): items[i] = (first vertex, end vertex, first CSR entry, end entry)
@@ -100,12 +99,12 @@ struct SellArgs {
     int32_t n_items;
     int32_t* queue;
 };
-cudaError_t launch_batch_sell(const SellArgs& a, int block, int lanes, int grid, cudaStream_t stream);
-int batch_sell_occupancy(int block, int lanes);
+cudaError_t launch_batch_sell(const SellArgs& a, int block, int chunk, int grid, cudaStream_t stream);
+int batch_sell_occupancy(int block, int chunk);
 
-// batched direct sweep; `tile` bounds the vertices of a work item (sizes the halo window)
-cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, int32_t tile, cudaStream_t stream);
-int batch_sweep_occupancy(int block, int lanes, int32_t tile, int32_t halo);  // resident CTAs per SM (0 on error)
+// batched work-queue sweep, rows read `chunk` (1, 2, 4 or 8) entries at a time
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int chunk, int grid, cudaStream_t stream);
+int batch_sweep_occupancy(int block, int chunk);  // resident CTAs per SM (0 on error)
 
 cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
                                      cudaStream_t stream);
@@ -124,6 +123,8 @@ cudaError_t launch_stop_check(const double* partials, double n, DevState* state,
 
 cudaError_t launch_gather_rows(int32_t n, const int32_t* new_to_old, const int32_t* rp_src, const int32_t* ci_src,
                                const int32_t* rp_dst, int32_t* ci_dst, const int32_t* map, cudaStream_t stream);
+// batched CSR: set bit 31 of row_ptr[v] for boundary vertices (read back with & 0x7fffffff)
+cudaError_t launch_flag_boundary_rows(int32_t n, const uint32_t* bits, int32_t* row_ptr, cudaStream_t stream);
 cudaError_t launch_map_ids(int64_t count, const int32_t* map, const int32_t* src, int32_t* dst,
                            cudaStream_t stream);
 cudaError_t launch_boundary_bits(int32_t n, const int32_t* new_to_old, const uint8_t* bnd_orig, uint32_t* bits,

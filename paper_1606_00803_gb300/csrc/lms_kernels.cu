@@ -19,8 +19,9 @@
 //         the division self-test.  GB300 runs FP64 at ~1/64 of the FP32 rate,
 //         and this is ~3 FP64 operations instead of a full division.
 //   FP32  coordinates are relative to the bounding-box centre and scaled to
-//         unit size; neighbour sums are Kahan-compensated; quality sums are
-//         reduced in FP64.
+//         unit size; neighbour sums are Kahan-compensated and the mean is the
+//         compensated sum times the round-to-nearest reciprocal of the count
+//         (within 1.5 ulp); quality sums are reduced in FP64.
 #include <cfloat>
 #include <cstdint>
 #include <type_traits>
@@ -32,6 +33,8 @@ namespace lms {
 
 namespace {
 using namespace dev;
+
+
 
 // Eq. 1 for one vertex.  FP64 reads the row kChunk entries at a time - all neighbour ids, then all
 // position gathers, then the sums in row order - so a thread keeps kChunk loads in flight while its FP64
@@ -72,9 +75,8 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
         r.x = div_by_count(dx_, e1 - e0, recip);
         r.y = div_by_count(dy_, e1 - e0, recip);
     } else {
-        const float d = static_cast<float>(e1 - e0);
-        r.x = __fdiv_rn(__fsub_rn(sx, cx), d);
-        r.y = __fdiv_rn(__fsub_rn(sy, cy), d);
+        r.x = mean_f32(sx, cx, e1 - e0);
+        r.y = mean_f32(sy, cy, e1 - e0);
     }
     double d2 = 0.0;
     if (want_disp) {
@@ -107,23 +109,17 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (want) record_disp(a.disp2, d2);
 }
 
-// Batched FP32 Jacobi: a persistent grid pulls vertex tiles from a device counter.
-//   LANES > 1: LANES lanes share one vertex; each Kahan-sums every LANES-th neighbour, then the
-//     partial sums are merged with shuffles (compensations folded in first).
-//   CHUNK > 1 (one lane per vertex): a row is read CHUNK entries at a time - all neighbour ids first,
-//     then all CHUNK position gathers, then the Kahan sums in row order - so each thread keeps CHUNK
-//     independent loads in flight instead of one.
-//   halo > 0: the positions of [tile start - halo, tile end + halo) are first loaded into shared
-//     memory with coalesced loads and neighbours inside that window are read from there.
-template <int LANES, int CHUNK>
+// Batched FP32 Jacobi: a persistent grid pulls vertex tiles (never crossing a mesh) from a device counter;
+// the next tile is requested while the current one is processed.  One thread per vertex; a row is read
+// CHUNK entries at a time - all neighbour ids, then all position gathers, then the Kahan sums in row
+// order - so a thread keeps CHUNK loads in flight.  The batch's row offsets carry the boundary flag in bit
+// 31 (row_ptr[v] | boundary(v) << 31), and row_ptr[v + 1] comes from the next lane, so a warp issues one
+// offset load per 32 vertices and no separate flag load.
+template <int CHUNK>
 __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
-    extern __shared__ float2 win_s[];
     __shared__ int32_t s_item[2];
     const float2* __restrict__ src = static_cast<const float2*>(a.src);
     float2* __restrict__ dst = static_cast<float2*>(a.dst);
-    const int group = threadIdx.x / LANES, sub = threadIdx.x % LANES;
-    const int groups = blockDim.x / LANES;
-    const int32_t halo = a.win_halo;
     int buf = 0;
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -132,80 +128,29 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
         if (item >= a.n_items) break;
         if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
         const int2 r = __ldg(a.items + item);
-        int32_t wlo = 0, wlen = 0;
-        if (halo > 0) {
-            wlo = max(r.x - halo, 0);
-            wlen = min(r.y + halo, a.v_end) - wlo;
-            for (int32_t k = threadIdx.x; k < wlen; k += blockDim.x) win_s[k] = __ldg(src + wlo + k);
-            __syncthreads();
-        }
-        auto fetch = [&](int32_t u) -> float2 {
-            const uint32_t o = static_cast<uint32_t>(u - wlo);
-            return o < static_cast<uint32_t>(wlen) ? win_s[o] : __ldg(src + u);
-        };
-        for (int32_t base = r.x; base < r.y; base += groups) {
-            const int32_t v = base + group;
-            bool active = v < r.y && !boundary_bit(a.bnd_bits, v);
-            int32_t e0 = 0, e1 = 0;
-            if (LANES == 1) {
-                // row_ptr[v + 1] is the next lane's row_ptr[v]; lanes past the tile end read
-                // row_ptr[tile end], and the last lane loads its own
-                const int32_t vv = v < r.y ? v : r.y;
-                e0 = __ldg(a.row_ptr + vv);
-                e1 = __shfl_down_sync(0xffffffffu, e0, 1);
-                if ((threadIdx.x & 31) == 31) e1 = v < r.y ? __ldg(a.row_ptr + v + 1) : e0;
-                if (!active) e1 = e0;
-            } else if (active) {
-                e0 = __ldg(a.row_ptr + v);
-                e1 = __ldg(a.row_ptr + v + 1);
-            }
+        for (int32_t base = r.x; base < r.y; base += blockDim.x) {  // uniform rounds: every lane shuffles
+            const int32_t v = base + threadIdx.x;
+            const int32_t f0 = __ldg(a.row_ptr + min(v, r.y));  // rows past the tile end read row_ptr[end]
+            int32_t f1 = __shfl_down_sync(0xffffffffu, f0, 1);
+            if ((threadIdx.x & 31) == 31) f1 = v < r.y ? __ldg(a.row_ptr + v + 1) : f0;
+            if (v >= r.y || f0 < 0) continue;  // past the end of the tile, or a boundary vertex
+            const int32_t e0 = f0, e1 = f1 & 0x7fffffff;
             float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-            if (CHUNK > 1) {
-                for (int32_t e = e0; e < e1; e += CHUNK) {
-                    int32_t u[CHUNK];
-                    float2 p[CHUNK];
+            for (int32_t e = e0; e < e1; e += CHUNK) {
+                int32_t u[CHUNK];
+                float2 p[CHUNK];
 #pragma unroll
-                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
 #pragma unroll
-                    for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? fetch(u[g]) : make_float2(0.f, 0.f);
+                for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int g = 0; g < CHUNK; ++g)
-                        if (u[g] >= 0) {
-                            kahan_add(sx, cx, p[g].x);
-                            kahan_add(sy, cy, p[g].y);
-                        }
-                }
-            } else {
-                for (int32_t e = e0 + sub; e < e1; e += LANES) {
-                    const float2 p = fetch(__ldg(a.col_idx + e));
-                    kahan_add(sx, cx, p.x);
-                    kahan_add(sy, cy, p.y);
-                }
+                for (int g = 0; g < CHUNK; ++g)
+                    if (u[g] >= 0) {
+                        kahan_add(sx, cx, p[g].x);
+                        kahan_add(sy, cy, p[g].y);
+                    }
             }
-            float tx = __fsub_rn(sx, cx), ty = __fsub_rn(sy, cy);
-            if (LANES > 1) {
-                float kx = 0.f, ky = 0.f;
-#pragma unroll
-                for (int o = 1; o < LANES; o <<= 1) {
-                    const float ox = __shfl_xor_sync(0xffffffffu, tx, o);
-                    const float oy = __shfl_xor_sync(0xffffffffu, ty, o);
-                    const float okx = __shfl_xor_sync(0xffffffffu, kx, o);
-                    const float oky = __shfl_xor_sync(0xffffffffu, ky, o);
-                    // two-sum of the partials, carrying the rounding error
-                    const float x = __fadd_rn(tx, ox), bx = __fsub_rn(x, tx);
-                    kx = __fadd_rn(__fadd_rn(kx, okx), __fadd_rn(__fsub_rn(tx, __fsub_rn(x, bx)), __fsub_rn(ox, bx)));
-                    tx = x;
-                    const float y = __fadd_rn(ty, oy), by = __fsub_rn(y, ty);
-                    ky = __fadd_rn(__fadd_rn(ky, oky), __fadd_rn(__fsub_rn(ty, __fsub_rn(y, by)), __fsub_rn(oy, by)));
-                    ty = y;
-                }
-                tx = __fadd_rn(tx, kx);
-                ty = __fadd_rn(ty, ky);
-            }
-            if (active && sub == 0) {
-                const float d = static_cast<float>(e1 - e0);
-                dst[v] = make_float2(__fdiv_rn(tx, d), __fdiv_rn(ty, d));
-            }
+            dst[v] = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
         }
         __syncthreads();
         buf ^= 1;
@@ -255,10 +200,7 @@ __global__ void __launch_bounds__(512) k_batch_sell(SellArgs a) {
                         ++cnt;
                     }
             }
-            if (v >= 0) {
-                const float d = static_cast<float>(cnt);
-                dst[v] = make_float2(__fdiv_rn(__fsub_rn(sx, cx), d), __fdiv_rn(__fsub_rn(sy, cy), d));
-            }
+            if (v >= 0) dst[v] = make_float2(mean_f32(sx, cx, cnt), mean_f32(sy, cy, cnt));
         }
         __syncthreads();
         buf ^= 1;
@@ -393,6 +335,12 @@ __global__ void k_gather_rows(int32_t n, const int32_t* __restrict__ new_to_old,
     }
 }
 
+// row_ptr[v] |= boundary(v) << 31 for v < n (row_ptr[n] keeps no flag)
+__global__ void k_flag_boundary_rows(int32_t n, const uint32_t* __restrict__ bits, int32_t* __restrict__ row_ptr) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && ((bits[v >> 5] >> (v & 31)) & 1u)) row_ptr[v] |= static_cast<int32_t>(0x80000000u);
+}
+
 __global__ void k_map_ids(int64_t count, const int32_t* __restrict__ map, const int32_t* __restrict__ src,
                           int32_t* __restrict__ dst) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -512,67 +460,55 @@ cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int b
     return cudaGetLastError();
 }
 
-size_t batch_window_bytes(int32_t tile, int32_t halo) { return halo > 0 ? 8 * size_t(tile + 2 * halo) : 0; }
-
 using BatchKernel = void (*)(SweepArgs);
 
-// lanes 1/2/4 with one entry at a time, or one lane with chunks of 4/8 (lanes = -4 / -8)
-BatchKernel batch_kernel(int lanes) {
-    switch (lanes) {
-        case 1: return k_batch_sweep<1, 1>;
-        case 2: return k_batch_sweep<2, 1>;
-        case 4: return k_batch_sweep<4, 1>;
-        case -4: return k_batch_sweep<1, 4>;
-        case -8: return k_batch_sweep<1, 8>;
+BatchKernel batch_kernel(int chunk) {
+    switch (chunk) {
+        case 1: return k_batch_sweep<1>;
+        case 2: return k_batch_sweep<2>;
+        case 4: return k_batch_sweep<4>;
+        case 8: return k_batch_sweep<8>;
         default: return nullptr;
     }
 }
 
-cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int lanes, int grid, int32_t tile, cudaStream_t stream) {
-    const BatchKernel k = batch_kernel(lanes);
-    if (k == nullptr) return cudaErrorInvalidValue;
-    const size_t smem = batch_window_bytes(tile, a.win_halo);
-    if (smem > 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-    }
-    k<<<grid, block, smem, stream>>>(a);
-    return cudaGetLastError();
-}
-
-using SellKernel = void (*)(SellArgs);
-
-SellKernel sell_kernel(int lanes) {
-    switch (lanes) {
-        case 1: return k_batch_sell<1>;
-        case -4: return k_batch_sell<4>;
-        case -8: return k_batch_sell<8>;
-        default: return nullptr;
-    }
-}
-
-cudaError_t launch_batch_sell(const SellArgs& a, int block, int lanes, int grid, cudaStream_t stream) {
-    const SellKernel k = sell_kernel(lanes);
+cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int chunk, int grid, cudaStream_t stream) {
+    const BatchKernel k = batch_kernel(chunk);
     if (k == nullptr) return cudaErrorInvalidValue;
     k<<<grid, block, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
-int batch_sell_occupancy(int block, int lanes) {
-    const SellKernel k = sell_kernel(lanes);
+int batch_sweep_occupancy(int block, int chunk) {
+    const BatchKernel k = batch_kernel(chunk);
     int n = 0;
     if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
     return n;
 }
 
-int batch_sweep_occupancy(int block, int lanes, int32_t tile, int32_t halo) {
-    const BatchKernel k = batch_kernel(lanes);
-    if (k == nullptr) return 0;
-    const size_t smem = batch_window_bytes(tile, halo);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return 0;
+using SellKernel = void (*)(SellArgs);
+
+SellKernel sell_kernel(int chunk) {
+    switch (chunk) {
+        case 1: return k_batch_sell<1>;
+        case 4: return k_batch_sell<4>;
+        case 8: return k_batch_sell<8>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_batch_sell(const SellArgs& a, int block, int chunk, int grid, cudaStream_t stream) {
+    const SellKernel k = sell_kernel(chunk);
+    if (k == nullptr) return cudaErrorInvalidValue;
+    k<<<grid, block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_sell_occupancy(int block, int chunk) {
+    const SellKernel k = sell_kernel(chunk);
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) == cudaSuccess ? n : 0;
+    if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
+    return n;
 }
 
 cudaError_t launch_tri_quality_exact(int32_t ntri, const int32_t* tri, const double* xy64, double* q_t,
@@ -614,6 +550,11 @@ cudaError_t launch_stop_check(const double* partials, double n, DevState* state,
 cudaError_t launch_gather_rows(int32_t n, const int32_t* new_to_old, const int32_t* rp_src, const int32_t* ci_src,
                                const int32_t* rp_dst, int32_t* ci_dst, const int32_t* map, cudaStream_t stream) {
     k_gather_rows<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, rp_src, ci_src, rp_dst, ci_dst, map);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_boundary_rows(int32_t n, const uint32_t* bits, int32_t* row_ptr, cudaStream_t stream) {
+    k_flag_boundary_rows<<<blocks_for(n, 256), 256, 0, stream>>>(n, bits, row_ptr);
     return cudaGetLastError();
 }
 

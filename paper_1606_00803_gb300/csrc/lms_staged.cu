@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(256) k_sweep_staged(StagedArgs a) {
             const bool active =
                 j < vb - va && !(a.bnd_bits != nullptr && ((bits[(v >> 5) - w0] >> (v & 31)) & 1u));
             if (active) {
-                const int32_t r0 = rp[j] - e0, r1 = rp[j + 1] - e0;
+                // (a batch's offsets carry a boundary flag in bit 31)
+                const int32_t r0 = (rp[j] & 0x7fffffff) - e0, r1 = (rp[j + 1] & 0x7fffffff) - e0;
                 V r;
                 if constexpr (FP64) {
                     double sx = 0.0, sy = 0.0;
@@ -235,9 +236,8 @@ __global__ void __launch_bounds__(256) k_sweep_staged(StagedArgs a) {
                         kahan_add(sx, cx, p.x);
                         kahan_add(sy, cy, p.y);
                     }
-                    const float d = static_cast<float>(r1 - r0);
-                    r.x = __fdiv_rn(__fsub_rn(sx, cx), d);
-                    r.y = __fdiv_rn(__fsub_rn(sy, cy), d);
+                    r.x = mean_f32(sx, cx, r1 - r0);
+                    r.y = mean_f32(sy, cy, r1 - r0);
                 }
                 if (want_disp) {
                     const V o = src[v];

@@ -286,15 +286,13 @@ def small_batch(count=10):
             for i, s in enumerate(sides)]
 
 
-@pytest.mark.parametrize("config", [(lms.KERNEL_STAGED, 256, 1, 256, 0), (lms.KERNEL_STAGED, 128, 1, 512, 0),
-                                    (lms.KERNEL_STAGED, 256, 1, 2048, 0), (lms.KERNEL_STAGED, 128, 1, 128, 0),
-                                    (lms.KERNEL_DIRECT, 256, 1, 256, 0), (lms.KERNEL_DIRECT, 512, 2, 1024, 0),
-                                    (lms.KERNEL_DIRECT, 128, 4, 512, 0), (lms.KERNEL_DIRECT, 256, 1, 4096, 0),
-                                    (lms.KERNEL_DIRECT, 128, 1, 256, 32), (lms.KERNEL_DIRECT, 256, 1, 1024, 512),
-                                    (lms.KERNEL_DIRECT, 512, 1, 2048, 4096), (lms.KERNEL_DIRECT, 128, -4, 512, 0),
-                                    (lms.KERNEL_DIRECT, 256, -8, 256, 32), (lms.KERNEL_DIRECT, 512, -8, 1024, 0),
-                                    (lms.KERNEL_SELL, 128, 1, 256, 0), (lms.KERNEL_SELL, 256, -4, 1024, 0),
-                                    (lms.KERNEL_SELL, 512, -8, 2048, 0), (lms.KERNEL_SELL, 128, -4, 128, 0)])
+@pytest.mark.parametrize("config", [(lms.KERNEL_STAGED, 256, 1, 256), (lms.KERNEL_STAGED, 128, 1, 512),
+                                    (lms.KERNEL_STAGED, 256, 1, 2048), (lms.KERNEL_STAGED, 128, 1, 128),
+                                    (lms.KERNEL_DIRECT, 256, 1, 256), (lms.KERNEL_DIRECT, 512, 2, 1024),
+                                    (lms.KERNEL_DIRECT, 128, 4, 512), (lms.KERNEL_DIRECT, 256, 8, 4096),
+                                    (lms.KERNEL_DIRECT, 128, 4, 128), (lms.KERNEL_SELL, 128, 1, 256),
+                                    (lms.KERNEL_SELL, 256, 4, 1024), (lms.KERNEL_SELL, 512, 8, 2048),
+                                    (lms.KERNEL_SELL, 128, 4, 128)])
 def test_batched_fp32_matches_oracle(config):
     meshes = small_batch()
     with lms.Batch(meshes, ordering=lms.RDR) as b:
@@ -314,7 +312,7 @@ def test_batched_autotune_keeps_positions():
         before = b.all_coords()
         cfg = b.autotune()
         assert cfg["kernel"] in (lms.KERNEL_DIRECT, lms.KERNEL_STAGED, lms.KERNEL_SELL)
-        assert cfg["block"] in (128, 256, 512) and cfg["lanes"] in (1, 2, 4, -4, -8)
+        assert cfg["block"] in (128, 256, 512) and cfg["chunk"] in (1, 2, 4, 8)
         assert np.array_equal(b.all_coords(), before)
         b.smooth(7)
         b.smooth(8)
