@@ -283,7 +283,8 @@ def per_ordering_table(hbm_peak):
 
 
 def large_table(hbm_peak):
-    """4096 x 4096 workload (~18.4M vertices): RANDOM vs RDR, FP64 vs FP32, Jacobi and coloured GS."""
+    """4096 x 4096 workload (~18.4M vertices, positions larger than L2): every ordering, FP64 vs FP32,
+    Jacobi and coloured GS."""
     import torch
     import meshgen
     import paper_1606_00803_gb300 as lms
@@ -292,10 +293,12 @@ def large_table(hbm_peak):
     n_int = int((m["is_boundary"] == 0).sum())
     stream = torch.cuda.current_stream()
     rows = {}
-    for oname, o in (("random", lms.RANDOM), ("rdr", lms.RDR)):
+    for oname, o in (("ori", lms.ORI), ("random", lms.RANDOM), ("bfs", lms.BFS), ("rdr", lms.RDR)):
         for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
             g = lms.Mesh.from_dict(m, p)
+            t0 = time.perf_counter()
             g.reorder(o, seed=meshgen.BASE_SEED + 7)
+            rows["%s/%s/reorder_ms" % (oname, pname)] = round((time.perf_counter() - t0) * 1e3, 1)
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
                 g.smooth(20, mode=mode)
                 torch.cuda.synchronize()

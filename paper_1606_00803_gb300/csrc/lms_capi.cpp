@@ -255,7 +255,11 @@ struct lms_mesh_s {
     int32_t n_items_all = 0;
     std::vector<int32_t> item_col_ofs;  // colour c: tiles [n_items_all + ofs[c], n_items_all + ofs[c+1])
     int32_t e_cap = 0;
-    int32_t* d_queue = nullptr;         // one tile counter per staged launch of a graph
+    int32_t* d_rpf = nullptr;           // row offsets of the current layout with the boundary flag in bit 31
+    int2* d_items2 = nullptr;           // FP32 Jacobi work-queue tiles over [0, n)
+    int64_t items2_cap = 0;
+    int32_t n_items2 = 0;
+    int32_t* d_queue = nullptr;         // one tile counter per work-queue launch of a graph
     int32_t queue_slots = 0;
     int32_t slot_next = 0;              // next counter while a graph is recorded
     int32_t* d_err = nullptr;           // set by a kernel whose bounded wait expired
@@ -343,6 +347,21 @@ int build_items(lms_mesh_s* h) {
     }
     LMS_CUDA(cudaMemcpyAsync(h->d_items4, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
                              h->stream));
+    // FP32 Jacobi work queue: tiles of kQueueTile vertices and row offsets carrying the boundary flag
+    constexpr int32_t kQueueTile = 512;
+    std::vector<int2> items2;
+    for (int32_t v = 0; v < h->n; v += kQueueTile) items2.push_back(make_int2(v, std::min(h->n, v + kQueueTile)));
+    if (int64_t(items2.size()) > h->items2_cap) {
+        const int64_t cap = int64_t(items2.size()) + 16;
+        LMS_TRY(h->arena.get(&h->d_items2, cap));
+        h->items2_cap = cap;
+    }
+    LMS_CUDA(cudaMemcpyAsync(h->d_items2, items2.data(), sizeof(int2) * items2.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    h->n_items2 = int32_t(items2.size());
+    LMS_CUDA(cudaMemcpyAsync(h->d_rpf, h->d_rp, sizeof(int32_t) * size_t(h->n + 1), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    LMS_TRY(check_launch(lms::launch_flag_boundary_rows(h->n, h->d_bits, h->d_rpf, h->stream), "flag_rows"));
     LMS_CUDA(cudaStreamSynchronize(h->stream));
     h->e_cap = e_cap;
     h->graphs.clear();
@@ -358,6 +377,11 @@ int ensure_queue(lms_mesh_s* h, int32_t slots) {
 }
 
 int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_JACOBI ? 1 : h->ncolours; }
+
+// FP32 Jacobi with the direct kernel runs on the work-queue sweep (rows in chunks of 4).
+bool uses_queue_sweep(const lms_mesh_s* h, int mode) {
+    return h->kernel == LMS_KERNEL_DIRECT && h->precision == LMS_FP32 && mode == LMS_JACOBI;
+}
 
 // Current positions as FP64 in the original labelling, in d_xy64.
 int positions_fp64_original(lms_mesh_s* h) {
@@ -453,6 +477,20 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
                                  "staged_sweep"));
         }
         return LMS_OK;
+    }
+    if (uses_queue_sweep(h, mode)) {
+        constexpr int kChunk = 4, kBlock = 128;
+        SweepArgs a = sweep_args(h, src, src ^ 1);
+        a.row_ptr = h->d_rpf;
+        a.items = h->d_items2;
+        a.n_items = h->n_items2;
+        if (h->slot_next >= h->queue_slots) return LMS_ERR_STATE;
+        a.queue = h->d_queue + h->slot_next++;
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        const int occ = std::max(1, lms::batch_sweep_occupancy(kBlock, kChunk));
+        const int grid = std::max(1, std::min(occ * h->sms, a.n_items));
+        return check_launch(lms::launch_batch_sweep(a, kBlock, kChunk, grid, s), "queue_sweep");
     }
     if (mode == LMS_JACOBI) {
         SweepArgs a = sweep_args(h, src, src ^ 1);
@@ -575,7 +613,7 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     int rc = LMS_OK;
     if ((rc = A.get(&h->d_rp0, n + 1)) || (rc = A.get(&h->d_ci0, std::max(1, h->nnz))) ||
         (rc = A.get(&h->d_tri0, t3)) || (rc = A.get(&h->d_vt_ptr, n + 1)) || (rc = A.get(&h->d_vt_idx, t3)) ||
-        (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1 + 8)) ||
+        (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1 + 8)) || (rc = A.get(&h->d_rpf, n + 1 + 8)) ||
         (rc = A.get(&h->d_ci, h->nnz + 8)) || (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
         (rc = A.get(&h->d_tmp, n)) || (rc = A.get(&h->d_bits, (n + 31) / 32 + 8)) || (rc = A.get(&h->d_err, 1)) ||
         (rc = A.get(&h->d_xy[0], vb)) || (rc = A.get(&h->d_xy[1], vb)) || (rc = A.get(&h->d_xy_swap, vb)) ||

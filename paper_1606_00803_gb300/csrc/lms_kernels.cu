@@ -115,11 +115,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 // order - so a thread keeps CHUNK loads in flight.  The batch's row offsets carry the boundary flag in bit
 // 31 (row_ptr[v] | boundary(v) << 31), and row_ptr[v + 1] comes from the next lane, so a warp issues one
 // offset load per 32 vertices and no separate flag load.
-template <int CHUNK>
+template <int CHUNK, bool EXTRAS>
 __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
     __shared__ int32_t s_item[2];
+    // EXTRAS (single-mesh sweeps): honour the stop flag and record the displacement when asked
+    if (EXTRAS && a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
     const float2* __restrict__ src = static_cast<const float2*>(a.src);
     float2* __restrict__ dst = static_cast<float2*>(a.dst);
+    const bool want_disp = EXTRAS && a.disp2 != nullptr;
     int buf = 0;
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
     __syncthreads();
@@ -133,24 +136,54 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
             const int32_t f0 = __ldg(a.row_ptr + min(v, r.y));  // rows past the tile end read row_ptr[end]
             int32_t f1 = __shfl_down_sync(0xffffffffu, f0, 1);
             if ((threadIdx.x & 31) == 31) f1 = v < r.y ? __ldg(a.row_ptr + v + 1) : f0;
-            if (v >= r.y || f0 < 0) continue;  // past the end of the tile, or a boundary vertex
-            const int32_t e0 = f0, e1 = f1 & 0x7fffffff;
-            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-            for (int32_t e = e0; e < e1; e += CHUNK) {
-                int32_t u[CHUNK];
-                float2 p[CHUNK];
+            if constexpr (!EXTRAS) {
+                if (v >= r.y || f0 < 0) continue;  // past the end of the tile, or a boundary vertex
+                const int32_t e0 = f0, e1 = f1 & 0x7fffffff;
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+                for (int32_t e = e0; e < e1; e += CHUNK) {
+                    int32_t u[CHUNK];
+                    float2 p[CHUNK];
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+                    for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g)
-                    if (u[g] >= 0) {
-                        kahan_add(sx, cx, p[g].x);
-                        kahan_add(sy, cy, p[g].y);
-                    }
+                    for (int g = 0; g < CHUNK; ++g)
+                        if (u[g] >= 0) {
+                            kahan_add(sx, cx, p[g].x);
+                            kahan_add(sy, cy, p[g].y);
+                        }
+                }
+                dst[v] = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
+                continue;
             }
-            dst[v] = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
+            double d2 = 0.0;
+            if (v < r.y && f0 >= 0) {  // inside the tile and not a boundary vertex
+                const int32_t e0 = f0, e1 = f1 & 0x7fffffff;
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+                for (int32_t e = e0; e < e1; e += CHUNK) {
+                    int32_t u[CHUNK];
+                    float2 p[CHUNK];
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int g = 0; g < CHUNK; ++g)
+                        if (u[g] >= 0) {
+                            kahan_add(sx, cx, p[g].x);
+                            kahan_add(sy, cy, p[g].y);
+                        }
+                }
+                const float2 q = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
+                if (EXTRAS && want_disp) {
+                    const float2 o = src[v];
+                    const double dx = static_cast<double>(__fsub_rn(q.x, o.x)), dy = static_cast<double>(__fsub_rn(q.y, o.y));
+                    d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                }
+                dst[v] = q;
+            }
+            if (EXTRAS && want_disp) record_disp(a.disp2, d2);
         }
         __syncthreads();
         buf ^= 1;
@@ -462,25 +495,25 @@ cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int b
 
 using BatchKernel = void (*)(SweepArgs);
 
-BatchKernel batch_kernel(int chunk) {
+BatchKernel batch_kernel(int chunk, bool extras) {
     switch (chunk) {
-        case 1: return k_batch_sweep<1>;
-        case 2: return k_batch_sweep<2>;
-        case 4: return k_batch_sweep<4>;
-        case 8: return k_batch_sweep<8>;
+        case 1: return extras ? k_batch_sweep<1, true> : k_batch_sweep<1, false>;
+        case 2: return extras ? k_batch_sweep<2, true> : k_batch_sweep<2, false>;
+        case 4: return extras ? k_batch_sweep<4, true> : k_batch_sweep<4, false>;
+        case 8: return extras ? k_batch_sweep<8, true> : k_batch_sweep<8, false>;
         default: return nullptr;
     }
 }
 
 cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int chunk, int grid, cudaStream_t stream) {
-    const BatchKernel k = batch_kernel(chunk);
+    const BatchKernel k = batch_kernel(chunk, a.state != nullptr || a.disp2 != nullptr);
     if (k == nullptr) return cudaErrorInvalidValue;
     k<<<grid, block, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 int batch_sweep_occupancy(int block, int chunk) {
-    const BatchKernel k = batch_kernel(chunk);
+    const BatchKernel k = batch_kernel(chunk, true);
     int n = 0;
     if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
     return n;
