@@ -64,15 +64,49 @@ void order_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_
         visited[next_root] = 1;
         out[written++] = next_root;
         while (read < written) {
-            int32_t v = out[read++];
-            nb.assign(col_idx + row_ptr[v], col_idx + row_ptr[v + 1]);
-            std::sort(nb.begin(), nb.end());
-            for (int32_t u : nb)
-                if (!visited[u]) {
-                    visited[u] = 1;
-                    out[written++] = u;
+            const int32_t v = out[read++];
+            const int32_t* r0 = col_idx + row_ptr[v];
+            const int32_t* r1 = col_idx + row_ptr[v + 1];
+            if (!std::is_sorted(r0, r1)) {  // neighbours are visited in ascending id
+                nb.assign(r0, r1);
+                std::sort(nb.begin(), nb.end());
+                r0 = nb.data();
+                r1 = nb.data() + nb.size();
+            }
+            for (const int32_t* it = r0; it != r1; ++it)
+                if (!visited[*it]) {
+                    visited[*it] = 1;
+                    out[written++] = *it;
                 }
         }
+    }
+}
+
+// Interior vertices in increasing (quality, id): a stable LSD radix sort (16-bit digits) of the
+// qualities' bit patterns, which order like the values for non-negative doubles; the input is in
+// ascending id, so equal qualities stay in ascending id.
+void sort_by_quality(std::vector<int32_t>& ids, const double* q) {
+    const size_t m = ids.size();
+    std::vector<uint64_t> key(m), key2(m);
+    std::vector<int32_t> ids2(m);
+    for (size_t i = 0; i < m; ++i) {
+        const double x = q[ids[i]] == 0.0 ? 0.0 : q[ids[i]];  // -0.0 sorts with +0.0
+        std::memcpy(&key[i], &x, sizeof(double));
+    }
+    std::vector<size_t> count(65537);
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 16 * pass;
+        std::fill(count.begin(), count.end(), 0);
+        for (size_t i = 0; i < m; ++i) count[((key[i] >> shift) & 0xffff) + 1]++;
+        if (count[(key[0] >> shift & 0xffff) + 1] == m) continue;  // one digit value only: already ordered
+        for (size_t d = 0; d < 65536; ++d) count[d + 1] += count[d];
+        for (size_t i = 0; i < m; ++i) {
+            const size_t at = count[(key[i] >> shift) & 0xffff]++;
+            key2[at] = key[i];
+            ids2[at] = ids[i];
+        }
+        key.swap(key2);
+        ids.swap(ids2);
     }
 }
 
@@ -85,7 +119,12 @@ void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     seeds.reserve(n);
     for (int32_t v = 0; v < n; ++v)
         if (!is_boundary[v]) seeds.push_back(v);
-    std::sort(seeds.begin(), seeds.end(), less);
+    bool non_negative = true;
+    for (int32_t v : seeds) non_negative = non_negative && q[v] >= 0.0;
+    if (non_negative && !seeds.empty())
+        sort_by_quality(seeds, q);
+    else
+        std::sort(seeds.begin(), seeds.end(), less);
 
     std::vector<uint8_t> done(n, 0), placed(n, 0);
     std::vector<int32_t> l;
