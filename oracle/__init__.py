@@ -13,6 +13,9 @@ Laplacian Mesh Smoothing"):
   order_random / order_bfs / order_rdr   Section 5.2.1, Algorithm 2
   relabel, color_greedy, color_sequence  storage under an ordering; the
                                   in-place order a coloured Gauss-Seidel follows
+  order_rbfs                      reversed BFS (Section 2, Munson and Hovland)
+  access_trace, reuse_distances, quantile   Section 2.2 / Fig. 1 reuse
+                                  distance of one sweep, Table 2 quantiles
 """
 import ctypes
 import os
@@ -24,7 +27,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lms_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liblms_oracle.so")
 
-ORI, RANDOM, BFS, RDR = 0, 1, 2, 3
+ORI, RANDOM, BFS, RDR, RBFS = 0, 1, 2, 3, 4
+DISTINCT, ACCESSES = 0, 1
 JACOBI, INPLACE = 0, 1
 
 
@@ -43,7 +47,9 @@ def build(force=False):
 _P_I32 = ctypes.POINTER(ctypes.c_int32)
 _P_U8 = ctypes.POINTER(ctypes.c_uint8)
 _P_F64 = ctypes.POINTER(ctypes.c_double)
+_P_I64 = ctypes.POINTER(ctypes.c_int64)
 _I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
 _handle = None
 
 
@@ -65,6 +71,10 @@ def _lib():
             "or_relabel": [_I32, _P_I32, _P_I32, _P_I32, _P_I32, _P_I32],
             "or_color_greedy": [_I32, _P_I32, _P_I32, _P_U8, _P_I32, _P_I32, _P_I32],
             "or_color_sequence": [_I32, _P_U8, _P_I32, _P_I32, _I32, _P_I32, _P_I32],
+            "or_order_rbfs": [_I32, _P_I32, _P_I32, _P_I32],
+            "or_access_trace": [_I32, _P_I32, _P_I32, _P_U8, _I32, _P_I32, _I32, _P_I32, _P_I64],
+            "or_reuse_distances": [_I64, _P_I32, _I32, _I32, _P_I64, _P_I64],
+            "or_quantile": [_I64, _P_I64, ctypes.c_double, _P_I64],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -176,8 +186,16 @@ def order_rdr(row_ptr, col_idx, is_boundary, q_v):
     return p
 
 
+def order_rbfs(row_ptr, col_idx):
+    row_ptr, col_idx = _i32(row_ptr), _i32(col_idx)
+    n = len(row_ptr) - 1
+    p = np.empty(n, np.int32)
+    _check(_lib().or_order_rbfs(n, _p(row_ptr, _P_I32), _p(col_idx, _P_I32), _p(p, _P_I32)), "order_rbfs")
+    return p
+
+
 def order(mesh, ordering, seed=0, q_v=None):
-    """Permutation new_to_old of a mesh dict for ORI/RANDOM/BFS/RDR (RDR keys from its coordinates)."""
+    """Permutation new_to_old of a mesh dict for ORI/RANDOM/BFS/RDR/RBFS (RDR keys from its coordinates)."""
     n = mesh["n"]
     if ordering == ORI:
         return np.arange(n, dtype=np.int32)
@@ -189,6 +207,8 @@ def order(mesh, ordering, seed=0, q_v=None):
         if q_v is None:
             q_v = vertex_quality(n, mesh["tri"], mesh["xy"])
         return order_rdr(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], q_v)
+    if ordering == RBFS:
+        return order_rbfs(mesh["row_ptr"], mesh["col_idx"])
     raise ValueError(ordering)
 
 
@@ -225,3 +245,33 @@ def gs_smooth(mesh, new_to_old, iters, tol=-1.0):
     seq = color_sequence(mesh["is_boundary"], new_to_old, colour, nc)
     return smooth(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], mesh["xy"], iters, mode=INPLACE, seq=seq,
                   tri=mesh["tri"] if tol >= 0 else None, tol=tol)
+
+
+def access_trace(row_ptr, col_idx, is_boundary, seq, with_vertex=True):
+    """Original ids accessed by one sweep visiting the interior vertices of seq (Fig. 3 pattern)."""
+    row_ptr, col_idx, bnd, seq = _i32(row_ptr), _i32(col_idx), _u8(is_boundary), _i32(seq)
+    n = len(row_ptr) - 1
+    ln = ctypes.c_int64()
+    args = (n, _p(row_ptr, _P_I32), _p(col_idx, _P_I32), _p(bnd, _P_U8), len(seq), _p(seq, _P_I32), int(with_vertex))
+    _check(_lib().or_access_trace(*args, None, ctypes.byref(ln)), "access_trace")
+    trace = np.empty(ln.value, np.int32)
+    _check(_lib().or_access_trace(*args, _p(trace, _P_I32), ctypes.byref(ln)), "access_trace")
+    return trace
+
+
+def reuse_distances(trace, n, measure=DISTINCT):
+    """Reuse distance of every non-first access of trace (elements 0..n-1), in trace order."""
+    trace = _i32(trace)
+    m = ctypes.c_int64()
+    dist = np.empty(len(trace), np.int64)
+    _check(_lib().or_reuse_distances(len(trace), _p(trace, _P_I32), n, measure, _p(dist, _P_I64), ctypes.byref(m)),
+           "reuse_distances")
+    return dist[: m.value]
+
+
+def quantile(values, X):
+    """Table 2's X quantile: the ceil(X m)-th smallest of the m values (clamped to [1, m])."""
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    out = ctypes.c_int64()
+    _check(_lib().or_quantile(len(values), _p(values, _P_I64), X, ctypes.byref(out)), "quantile")
+    return out.value

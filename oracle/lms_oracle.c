@@ -31,6 +31,13 @@
  *   or_color_greedy - first-fit colouring of the interior vertices in
  *       storage order; the sequence "colour by colour, storage order inside a
  *       colour" is the in-place sweep that a coloured Gauss-Seidel reproduces.
+ *   or_order_rbfs - the reversed breadth-first order (BFS visit order read
+ *       backwards) that Section 2 reports from Munson and Hovland's study.
+ *   or_access_trace / or_reuse_distances / or_quantile - Section 2.2's reuse
+ *       distance over the data accesses of one sweep (Fig. 3: a vertex, then
+ *       its neighbours), and the quantiles of Table 2 (the X quantile is the
+ *       smallest value with at least a fraction X of the population at or
+ *       below it).
  *
  * Readings where the paper is silent (the same list is kept with the design
  * notes):
@@ -49,7 +56,17 @@
  *   - RANDOM is a Fisher-Yates shuffle driven by splitmix64 (Steele, Lea &
  *     Flood, OOPSLA 2014) seeded with the given seed;
  *   - the stopping rule stops after sweep k when Q_k >= goal or
- *     Q_k - Q_{k-1} < tol (a signed difference).
+ *     Q_k - Q_{k-1} < tol (a signed difference);
+ *   - the access trace of a sweep visits the interior vertices in the given
+ *     sequence; for each it lists the vertex itself (optional) and then its
+ *     stored row; an element is a vertex.  Two measures of the distance
+ *     between consecutive accesses to one element: the number of distinct
+ *     elements accessed in between (Section 2.2, Fig. 1) and the number of
+ *     accesses in between (Table 2's maxima exceed the vertex count, which
+ *     only this measure allows).  First accesses have no reuse distance and
+ *     are left out of the population;
+ *   - the quantile index is k = ceil(X * m) in double precision, clamped to
+ *     [1, m], over the m sorted distances (the k-th smallest is returned).
  */
 #include <math.h>
 #include <stdint.h>
@@ -275,6 +292,18 @@ int or_order_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int3
     return OR_OK;
 }
 
+/* Reversed BFS: the BFS visit order read from its last vertex to its first. */
+int or_order_rbfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* new_to_old) {
+    if (n <= 0 || !new_to_old) return OR_ERR_ARG;
+    int32_t* fwd = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!fwd) return OR_ERR_OOM;
+    int rc = or_order_bfs(n, row_ptr, col_idx, fwd);
+    if (rc == OR_OK)
+        for (int32_t k = 0; k < n; ++k) new_to_old[k] = fwd[n - 1 - k];
+    free(fwd);
+    return rc;
+}
+
 /* RDR sort key: (quality, id) ascending */
 static const double* g_key_q;
 static int key_less(int32_t a, int32_t b) {
@@ -427,5 +456,87 @@ int or_color_sequence(int32_t n, const uint8_t* is_boundary, const int32_t* new_
             if (!is_boundary[v] && colour[v] == c) seq[m++] = v;
         }
     *nseq = m;
+    return OR_OK;
+}
+
+/*
+ * The data accesses of one sweep over the interior vertices of seq (original
+ * ids, in visiting order): for each, the vertex itself when with_vertex != 0,
+ * then the entries of its stored row.  trace receives original ids; *len the
+ * count.  trace may be NULL to count only.
+ */
+int or_access_trace(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    int32_t nseq, const int32_t* seq, int32_t with_vertex, int32_t* trace, int64_t* len) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || nseq < 0 || (nseq > 0 && !seq) || !len) return OR_ERR_ARG;
+    int64_t t = 0;
+    for (int32_t k = 0; k < nseq; ++k) {
+        int32_t v = seq[k];
+        if (v < 0 || v >= n) return OR_ERR_ARG;
+        if (is_boundary[v]) continue;
+        if (with_vertex) {
+            if (trace) trace[t] = v;
+            ++t;
+        }
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            if (trace) trace[t] = col_idx[e];
+            ++t;
+        }
+    }
+    *len = t;
+    return OR_OK;
+}
+
+/*
+ * Reuse distances of a trace over elements 0..n-1, by direct inspection: for
+ * the access at time t to element x whose previous access was at time p, the
+ * accesses at times p+1 .. t-1 are walked and either counted (measure 1) or
+ * their distinct elements counted (measure 0).  dist receives one value per
+ * access that has a previous access, in trace order; *m their count.
+ */
+int or_reuse_distances(int64_t len, const int32_t* trace, int32_t n, int32_t measure, int64_t* dist, int64_t* m) {
+    if (len < 0 || (len > 0 && !trace) || n <= 0 || (measure != 0 && measure != 1) || !m) return OR_ERR_ARG;
+    int64_t* last = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!last || !stamp) { free(last); free(stamp); return OR_ERR_OOM; }
+    for (int32_t i = 0; i < n; ++i) { last[i] = -1; stamp[i] = -1; }
+    int64_t cnt = 0;
+    for (int64_t t = 0; t < len; ++t) {
+        int32_t x = trace[t];
+        if (x < 0 || x >= n) { free(last); free(stamp); return OR_ERR_ARG; }
+        int64_t p = last[x];
+        if (p >= 0) {
+            int64_t d = 0;
+            for (int64_t s = p + 1; s < t; ++s) {
+                if (measure == 1) { ++d; continue; }
+                if (stamp[trace[s]] != t) { stamp[trace[s]] = t; ++d; }
+            }
+            if (dist) dist[cnt] = d;
+            ++cnt;
+        }
+        last[x] = t;
+    }
+    free(last); free(stamp);
+    *m = cnt;
+    return OR_OK;
+}
+
+static int cmp_int64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Table 2's X quantile of m values: the k-th smallest, k = ceil(X * m) clamped to [1, m]. */
+int or_quantile(int64_t m, const int64_t* values, double X, int64_t* out) {
+    if (m <= 0 || !values || !out || !(X >= 0.0 && X <= 1.0)) return OR_ERR_ARG;
+    int64_t* s = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    if (!s) return OR_ERR_OOM;
+    memcpy(s, values, sizeof(int64_t) * (size_t)m);
+    qsort(s, (size_t)m, sizeof(int64_t), cmp_int64);
+    double km = ceil(X * (double)m);
+    int64_t k = (int64_t)km;
+    if (k < 1) k = 1;
+    if (k > m) k = m;
+    *out = s[k - 1];
+    free(s);
     return OR_OK;
 }
