@@ -62,6 +62,12 @@ extern "C" {
                         restarting at the smallest unvisited id */
 #define LMS_RDR 3    /* Algorithm 2: walks from the worst-quality interior vertex, appending
                         unordered neighbours by increasing (quality, id) */
+#define LMS_RBFS 4   /* reversed BFS: the LMS_BFS visit order read backwards (the ordering Section 2
+                        reports from Munson and Hovland's study) */
+
+/* reuse-distance measures (lms_reuse_profile) */
+#define LMS_REUSE_DISTINCT 0 /* distinct elements accessed between two accesses to one element (Section 2.2) */
+#define LMS_REUSE_ACCESSES 1 /* accesses between them (the measure Table 2's maxima imply) */
 
 /* sweep modes */
 #define LMS_JACOBI 0     /* all interior vertices read the previous sweep's positions (ping-pong) */
@@ -121,6 +127,25 @@ int lms_validate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
  */
 int lms_order_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                    const double* q_v, int ordering, uint64_t seed, int32_t* new_to_old);
+
+/*
+ * Reuse-distance profile of one sweep (Section 2.2, Fig. 1, Table 2).  The
+ * trace visits the interior vertices in storage order new_to_old (NULL: the
+ * identity) and lists, for each, the vertex itself when with_vertex != 0 and
+ * then its stored row (the access pattern of Fig. 3); elements are vertices.
+ * Every access that repeats an element gets a reuse distance (measure =
+ * LMS_REUSE_DISTINCT or LMS_REUSE_ACCESSES); first accesses get none.
+ * Outputs (each may be NULL): out_q[i] = the q[i] quantile for i < nq, the
+ * ceil(q[i] m)-th smallest of the m distances (clamped to [1, m]; -1 when m = 0;
+ * q[i] in [0, 1]); *mean; *n_accesses = trace length; *n_reuses = m;
+ * hist[33]: hist[0] counts distance 0, hist[b] distances in [2^(b-1), 2^b).
+ * Cost O(T log T) time and 8 T bytes for a trace of T accesses (T < 2^32).
+ * Returns LMS_ERR_ARG (NULL input, bad enum, q outside [0, 1], new_to_old not a
+ * permutation), LMS_ERR_CSR or LMS_ERR_OOM.  [host]
+ */
+int lms_reuse_profile(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                      const int32_t* new_to_old, int32_t with_vertex, int32_t measure, int32_t nq, const double* q,
+                      int64_t* out_q, double* mean, int64_t* n_accesses, int64_t* n_reuses, int64_t* hist);
 
 /*
  * First-fit colouring of the interior vertices visited in storage order

@@ -23,9 +23,10 @@ from . import _build
 
 FP64, FP32 = 0, 1
 KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
-ORI, RANDOM, BFS, RDR = 0, 1, 2, 3
+ORI, RANDOM, BFS, RDR, RBFS = 0, 1, 2, 3, 4
 JACOBI, COLORED_GS = 0, 1
-ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR}
+REUSE_DISTINCT, REUSE_ACCESSES = 0, 1
+ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS}
 MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS}
 PRECISIONS = {"fp64": FP64, "fp32": FP32}
 
@@ -65,6 +66,7 @@ _SIGS = {
     "lms_validate": ([_I32, _P, _P, _P, _I32, _P], ctypes.c_int),
     "lms_order_host": ([_I32, _P, _P, _P, _P, ctypes.c_int, _U64, _P], ctypes.c_int),
     "lms_color_host": ([_I32, _P, _P, _P, _P, _P, _PI32], ctypes.c_int),
+    "lms_reuse_profile": ([_I32, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P, _PD, _PI64, _PI64, _P], ctypes.c_int),
     "lms_create": ([_I32, _P, _P, _P, _P, _I32, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "lms_reorder": ([_P, ctypes.c_int, _U64], ctypes.c_int),
     "lms_smooth": ([_P, _I32, ctypes.c_int, _D, _PI32], ctypes.c_int),
@@ -199,7 +201,7 @@ def validate(row_ptr, col_idx, is_boundary, tri=None):
 
 
 def order_host(row_ptr, col_idx, is_boundary, ordering, seed=0, q_v=None):
-    """lms_order_host: new_to_old of ORI / RANDOM / BFS / RDR (RDR needs q_v)."""
+    """lms_order_host: new_to_old of ORI / RANDOM / BFS / RDR / RBFS (RDR needs q_v)."""
     rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
     q = _arr(q_v, np.float64) if q_v is not None else None
     n = len(rp) - 1
@@ -218,6 +220,25 @@ def color_host(row_ptr, col_idx, is_boundary, new_to_old):
     _check(_lib().lms_color_host(n, _ptr(rp), _ptr(ci), _ptr(b), _ptr(p), _ptr(colour), ctypes.byref(nc)),
            "lms_color_host")
     return colour, nc.value
+
+
+def reuse_profile(row_ptr, col_idx, is_boundary, new_to_old=None, with_vertex=True, measure=REUSE_DISTINCT,
+                  quantiles=(0.5, 0.75, 0.9, 1.0)):
+    """lms_reuse_profile: reuse distances of one sweep's access trace (Section 2.2, Table 2).
+
+    Returns a dict: quantiles {X: value}, mean, accesses (trace length), reuses (accesses with
+    a previous access of the same element) and hist (33 log2 buckets)."""
+    rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
+    p = _arr(new_to_old, np.int32) if new_to_old is not None else None
+    qs = _arr(list(quantiles), np.float64)
+    out_q = np.empty(len(qs), np.int64)
+    hist = np.zeros(33, np.int64)
+    mean, acc, reu = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib().lms_reuse_profile(len(rp) - 1, _ptr(rp), _ptr(ci), _ptr(b), _ptr(p), int(bool(with_vertex)),
+                                    int(measure), len(qs), _ptr(qs), _ptr(out_q), ctypes.byref(mean),
+                                    ctypes.byref(acc), ctypes.byref(reu), _ptr(hist)), "lms_reuse_profile")
+    return {"quantiles": {float(x): int(v) for x, v in zip(qs, out_q)}, "mean": mean.value, "accesses": acc.value,
+            "reuses": reu.value, "hist": hist}
 
 
 def selftest_div64(s, d):

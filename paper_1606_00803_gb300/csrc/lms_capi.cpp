@@ -675,7 +675,7 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
 }
 
 int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
-    if (!h || ordering < LMS_ORI || ordering > LMS_RDR) return LMS_ERR_ARG;
+    if (!h || ordering < LMS_ORI || ordering > LMS_RBFS) return LMS_ERR_ARG;
     if (ordering == LMS_RDR && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
     std::vector<double> q;
@@ -1206,7 +1206,7 @@ extern "C" {
 
 int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint64_t seed, void* cuda_stream,
                      lms_batch* out) {
-    if (!out || !meshes || k <= 0 || ordering < LMS_ORI || ordering > LMS_RDR) return LMS_ERR_ARG;
+    if (!out || !meshes || k <= 0 || ordering < LMS_ORI || ordering > LMS_RBFS) return LMS_ERR_ARG;
     *out = nullptr;
     // validate in parallel
     std::vector<int> status(k, LMS_OK);

@@ -12,9 +12,19 @@
 //          every vertex, not only the interior ones its proof covers);
 //   BFS  - from vertex 0, neighbours in ascending id, restart at the smallest
 //          unvisited id;
-//   RANDOM - Fisher-Yates, i = n-1 .. 1, j = splitmix64() mod (i+1).
+//   RANDOM - Fisher-Yates, i = n-1 .. 1, j = splitmix64() mod (i+1);
+//   RBFS - the BFS visit order read backwards (the reversed breadth-first order
+//          Section 2 reports from Munson and Hovland).
+//
+// The reuse-distance profile follows Section 2.2 and Table 2: the access trace of one sweep
+// (each interior vertex in storage order, optionally itself, then its stored row - the pattern of
+// Fig. 3), the reuse distance of each access that repeats an element (distinct elements, or
+// accesses, in between), and Table 2's quantiles (the k-th smallest, k = ceil(X m) in double,
+// clamped to [1, m]).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <new>
 #include <deque>
 #include <vector>
 
@@ -159,6 +169,106 @@ void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     }
     for (int32_t v = 0; v < n; ++v) place(v);  // vertices no walk reached, ascending id
 }
+// Reuse distances of one sweep's access trace.  Distinct-element distances use a Fenwick tree over
+// access times holding a 1 at the latest access of every element seen so far: for an access at
+// time t to an element last accessed at time p, the elements accessed in between are the marks
+// after p, i.e. (elements seen) - prefix(p).
+int reuse_profile(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                  const int32_t* new_to_old, int32_t with_vertex, int32_t measure, int32_t nq, const double* q,
+                  int64_t* out_q, double* mean, int64_t* n_accesses, int64_t* n_reuses, int64_t* hist) {
+    if (n <= 0 || !row_ptr || !is_boundary || (measure != LMS_REUSE_DISTINCT && measure != LMS_REUSE_ACCESSES) ||
+        nq < 0 || (nq > 0 && (!q || !out_q)))
+        return LMS_ERR_ARG;
+    for (int32_t i = 0; i < nq; ++i)
+        if (!(q[i] >= 0.0 && q[i] <= 1.0)) return LMS_ERR_ARG;
+    if (row_ptr[0] != 0) return LMS_ERR_CSR;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return LMS_ERR_CSR;
+    const int32_t nnz = row_ptr[n];
+    if (nnz > 0 && !col_idx) return LMS_ERR_ARG;
+    for (int32_t e = 0; e < nnz; ++e)
+        if (col_idx[e] < 0 || col_idx[e] >= n) return LMS_ERR_CSR;
+    if (new_to_old) {
+        std::vector<uint8_t> hit(n, 0);
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t v = new_to_old[k];
+            if (v < 0 || v >= n || hit[v]) return LMS_ERR_ARG;
+            hit[v] = 1;
+        }
+    }
+    int64_t len = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (!is_boundary[v]) len += row_len(row_ptr, v) + (with_vertex ? 1 : 0);
+    if (len >= (int64_t(1) << 32)) return LMS_ERR_ARG;
+
+    std::vector<int64_t> last(n, -1);
+    std::vector<uint32_t> dist;
+    dist.reserve(size_t(len));
+    std::vector<uint32_t> bit;  // Fenwick tree over times 1..len (distinct measure only)
+    if (measure == LMS_REUSE_DISTINCT) bit.assign(size_t(len) + 1, 0u);
+    int64_t t = 0, seen = 0;
+    auto access = [&](int32_t x) {
+        const int64_t p = last[x];
+        if (p >= 0) {
+            uint32_t d;
+            if (measure == LMS_REUSE_ACCESSES) {
+                d = uint32_t(t - p - 1);
+            } else {
+                int64_t before = 0;  // marks at times <= p
+                for (int64_t i = p + 1; i > 0; i -= i & -i) before += bit[i];
+                d = uint32_t(seen - before);
+                for (int64_t i = p + 1; i <= len; i += i & -i) --bit[i];
+            }
+            dist.push_back(d);
+        } else {
+            ++seen;
+        }
+        if (measure == LMS_REUSE_DISTINCT)
+            for (int64_t i = t + 1; i <= len; i += i & -i) ++bit[i];
+        last[x] = t++;
+    };
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t v = new_to_old ? new_to_old[k] : k;
+        if (is_boundary[v]) continue;
+        if (with_vertex) access(v);
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) access(col_idx[e]);
+    }
+    std::vector<uint32_t>().swap(bit);
+    const int64_t m = int64_t(dist.size());
+    if (n_accesses) *n_accesses = len;
+    if (n_reuses) *n_reuses = m;
+    if (hist) {  // bucket 0: distance 0; bucket b >= 1: distances in [2^(b-1), 2^b)
+        std::fill(hist, hist + 33, 0);
+        for (uint32_t d : dist) ++hist[d == 0 ? 0 : 32 - __builtin_clz(d)];
+    }
+    if (mean) {
+        uint64_t sum = 0;
+        for (uint32_t d : dist) sum += d;
+        *mean = m > 0 ? double(sum) / double(m) : 0.0;
+    }
+    // quantiles in increasing k: each selection narrows the range of the next
+    std::vector<std::pair<int64_t, int32_t>> ks;
+    for (int32_t i = 0; i < nq; ++i) {
+        int64_t k = int64_t(std::ceil(q[i] * double(m)));
+        ks.push_back({std::min(std::max(k, int64_t(1)), std::max(m, int64_t(1))), i});
+    }
+    std::sort(ks.begin(), ks.end());
+    auto lo = dist.begin();
+    for (const auto& [k, i] : ks) {
+        if (m == 0) {
+            out_q[i] = -1;
+            continue;
+        }
+        auto it = dist.begin() + (k - 1);
+        if (it >= lo) {
+            std::nth_element(lo, it, dist.end());
+            lo = it;
+        }
+        out_q[i] = int64_t(*it);
+    }
+    return LMS_OK;
+}
+
 }  // namespace
 
 void set_error_detail(const std::string& s) { g_detail = s; }
@@ -217,6 +327,11 @@ int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
         case LMS_RDR:
             if (!q_v || !is_boundary || (!col_idx && row_ptr[n] > 0)) return LMS_ERR_ARG;
             order_rdr(n, row_ptr, col_idx, is_boundary, q_v, new_to_old);
+            return LMS_OK;
+        case LMS_RBFS:
+            if (!col_idx && row_ptr[n] > 0) return LMS_ERR_ARG;
+            order_bfs(n, row_ptr, col_idx, new_to_old);
+            std::reverse(new_to_old, new_to_old + n);
             return LMS_OK;
         default:
             return LMS_ERR_ARG;
@@ -294,6 +409,17 @@ int lms_order_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
 int lms_color_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours) {
     return lms::colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour, ncolours);
+}
+
+int lms_reuse_profile(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                      const int32_t* new_to_old, int32_t with_vertex, int32_t measure, int32_t nq, const double* q,
+                      int64_t* out_q, double* mean, int64_t* n_accesses, int64_t* n_reuses, int64_t* hist) {
+    try {
+        return lms::reuse_profile(n, row_ptr, col_idx, is_boundary, new_to_old, with_vertex, measure, nq, q, out_q,
+                                  mean, n_accesses, n_reuses, hist);
+    } catch (const std::bad_alloc&) {
+        return LMS_ERR_OOM;
+    }
 }
 
 }  // extern "C"

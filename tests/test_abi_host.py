@@ -86,7 +86,7 @@ def test_validate_rejects_bad_meshes():
 
 
 @pytest.mark.parametrize("side", [6, 20, 57])
-@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR])
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS])
 def test_host_ordering_matches_oracle(side, ordering):
     m = meshgen.workload(1, side=side)
     q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
@@ -138,3 +138,52 @@ def test_host_entry_points_reject_bad_arguments():
         lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], 7)
     with pytest.raises(lms.LmsError):
         lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.RDR, q_v=None)
+
+
+QS = (0.0, 0.01, 0.5, 0.75, 0.9, 0.99, 1.0)
+
+
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS])
+@pytest.mark.parametrize("with_vertex", [True, False])
+@pytest.mark.parametrize("measure", [lms.REUSE_DISTINCT, lms.REUSE_ACCESSES])
+def test_reuse_profile_matches_oracle(ordering, with_vertex, measure):
+    m = meshgen.workload(1, side=37)
+    p = oracle.order(m, ordering, seed=21)
+    t = oracle.access_trace(m["row_ptr"], m["col_idx"], m["is_boundary"], p, with_vertex)
+    d = oracle.reuse_distances(t, m["n"], measure)
+    r = lms.reuse_profile(m["row_ptr"], m["col_idx"], m["is_boundary"], p, with_vertex, measure, QS)
+    assert [r["quantiles"][x] for x in QS] == [oracle.quantile(d, x) for x in QS]
+    assert r["accesses"] == len(t) and r["reuses"] == len(d)
+    assert r["mean"] == int(d.sum()) / len(d)
+    hist = np.zeros(33, np.int64)
+    np.add.at(hist, [0 if x == 0 else int(x).bit_length() for x in d.tolist()], 1)
+    assert np.array_equal(r["hist"], hist)
+
+
+def test_reuse_profile_identity_default_and_edge_cases():
+    m = meshgen.workload(1, side=12)
+    a = lms.reuse_profile(m["row_ptr"], m["col_idx"], m["is_boundary"])
+    b = lms.reuse_profile(m["row_ptr"], m["col_idx"], m["is_boundary"], np.arange(m["n"]))
+    assert a["quantiles"] == b["quantiles"] and a["mean"] == b["mean"]
+    # every vertex on the boundary: empty trace, no reuses
+    r = lms.reuse_profile(m["row_ptr"], m["col_idx"], np.ones(m["n"], np.uint8))
+    assert r["accesses"] == 0 and r["reuses"] == 0 and set(r["quantiles"].values()) == {-1}
+    # one interior vertex: its row has no repeated element, the vertex itself is not in its row
+    r = lms.reuse_profile(m["row_ptr"], m["col_idx"], (np.arange(m["n"]) != 13).astype(np.uint8))
+    assert r["reuses"] == 0
+
+
+def test_reuse_profile_rejects_bad_arguments():
+    m = meshgen.workload(1, side=10)
+    args = (m["row_ptr"], m["col_idx"], m["is_boundary"])
+    bad_perm = np.arange(m["n"])
+    bad_perm[3] = 4
+    for kw in ({"new_to_old": bad_perm}, {"measure": 2}, {"quantiles": (1.5,)}, {"quantiles": (-0.1,)}):
+        with pytest.raises(lms.LmsError) as e:
+            lms.reuse_profile(*args, **kw)
+        assert e.value.status == -1
+    ci = m["col_idx"].copy()
+    ci[0] = m["n"]
+    with pytest.raises(lms.LmsError) as e:
+        lms.reuse_profile(m["row_ptr"], ci, m["is_boundary"])
+    assert e.value.status == -2

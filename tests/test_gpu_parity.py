@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 2e-6
-ORDERINGS = [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR]
+ORDERINGS = [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS]
 
 
 def diag(m):
@@ -304,6 +304,18 @@ def test_batched_fp32_matches_oracle(config):
             assert err(b.coords(i), want, m) <= TOL32
         allc = b.all_coords()
         assert np.array_equal(allc[b.offsets[3]:b.offsets[4]], b.coords(3))
+
+
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.BFS, lms.RBFS])
+def test_batched_orderings(ordering):
+    meshes = small_batch(5)
+    with lms.Batch(meshes, ordering=ordering) as b:
+        b.set_config(lms.KERNEL_DIRECT, 128, 4, 512)
+        b.smooth(30)
+        for i, m in enumerate(meshes):
+            assert np.array_equal(b.permutation(i), oracle.order(m, ordering))
+            want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 30)
+            assert err(b.coords(i), want, m) <= TOL32
 
 
 def test_batched_autotune_keeps_positions():
