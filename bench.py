@@ -33,6 +33,7 @@ METRIC = "vertex updates/s and % HBM roofline: FP32 batched vs FP64 plain, per o
 UNIT = "vertex updates/s"
 SWEEPS_PER_STEP = 50
 PER_ORDERING_SWEEPS = 100
+ORDERINGS = (("ori", 0), ("random", 1), ("bfs", 2), ("rdr", 3), ("rbfs", 4))  # LMS_ORI .. LMS_RBFS
 L2_BYTES = 129 * 2 ** 20
 FP64_OPS_PEAK_NOTE = "2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s counting an FMA as 2)"
 
@@ -230,6 +231,21 @@ def time_graph(fn, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def reuse_row(lms, m, new_to_old, both):
+    """Table 2-style reuse-distance quantiles of one sweep's access trace (each interior vertex, then its
+    row) under an ordering, distinct-element measure (and the access-count measure when both)."""
+    row = {}
+    for name, measure in (("distinct", lms.REUSE_DISTINCT), ("accesses", lms.REUSE_ACCESSES))[: 2 if both else 1]:
+        t0 = time.perf_counter()
+        r = lms.reuse_profile(m["row_ptr"], m["col_idx"], m["is_boundary"], new_to_old, True, measure,
+                              (0.5, 0.75, 0.9, 1.0))
+        row[name] = dict(q50=r["quantiles"][0.5], q75=r["quantiles"][0.75], q90=r["quantiles"][0.9],
+                         q100=r["quantiles"][1.0], mean=round(r["mean"], 1),
+                         analysis_ms=round((time.perf_counter() - t0) * 1e3, 1))
+        row["accesses_per_sweep"] = r["accesses"]
+    return row
+
+
 def per_ordering_table(hbm_peak):
     """1024 x 1024 workload: every ordering x {FP64, FP32} x {Jacobi, coloured GS}, 100 sweeps."""
     import torch
@@ -242,12 +258,14 @@ def per_ordering_table(hbm_peak):
     nnz_int = int(deg[m["is_boundary"] == 0].sum())
     stream = torch.cuda.current_stream()
     rows = {}
-    for oname, o in (("ori", lms.ORI), ("random", lms.RANDOM), ("bfs", lms.BFS), ("rdr", lms.RDR)):
+    for oname, o in ORDERINGS:
         for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
             g = lms.Mesh.from_dict(m, p)
             t0 = time.perf_counter()
             g.reorder(o, seed=meshgen.BASE_SEED + 7)
             reorder_ms = (time.perf_counter() - t0) * 1e3
+            if p == lms.FP64:
+                rows["%s/reuse" % oname] = reuse_row(lms, m, g.permutation(), both=True)
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
                 g.smooth(PER_ORDERING_SWEEPS, mode=mode)  # warm-up + graph capture
                 torch.cuda.synchronize()
@@ -293,12 +311,14 @@ def large_table(hbm_peak):
     n_int = int((m["is_boundary"] == 0).sum())
     stream = torch.cuda.current_stream()
     rows = {}
-    for oname, o in (("ori", lms.ORI), ("random", lms.RANDOM), ("bfs", lms.BFS), ("rdr", lms.RDR)):
+    for oname, o in ORDERINGS:
         for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
             g = lms.Mesh.from_dict(m, p)
             t0 = time.perf_counter()
             g.reorder(o, seed=meshgen.BASE_SEED + 7)
             rows["%s/%s/reorder_ms" % (oname, pname)] = round((time.perf_counter() - t0) * 1e3, 1)
+            if p == lms.FP64:
+                rows["%s/reuse" % oname] = reuse_row(lms, m, g.permutation(), both=False)
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
                 g.smooth(20, mode=mode)
                 torch.cuda.synchronize()
@@ -440,11 +460,13 @@ def run_ours(args, dist):
 
 
 def kernel_source_digest():
-    """sha256 over the library's device and host sources: any change makes recorded counters stale."""
+    """sha256 over the library's device sources: any change makes recorded counters stale."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1606_00803_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
+        if not name.endswith((".cu", ".cuh")) and name != "lms_internal.h":
+            continue  # host-only sources do not change what a kernel moves
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
