@@ -283,6 +283,48 @@ struct lms_mesh_s {
 
 namespace {
 
+// Breadth-first orderings on the device (k_bfs) of k graphs with vertex offsets voff (host; NULL:
+// one graph of n vertices) over the device CSR rp/ci with global ids; out (host, [n]) receives the
+// global new_to_old.  Scratch comes from the allocator and is released before returning.
+int device_bfs(const Allocator& al, cudaStream_t s, const int32_t* rp, const int32_t* ci, int32_t n,
+               int32_t k, const int64_t* voff, int32_t* out) {
+    Arena tmp;
+    tmp.al = al;
+    tmp.stream = s;
+    lms::BfsArgs a{};
+    int32_t* d_voff = nullptr;
+    int rc;
+    if ((rc = tmp.get(&a.out, n)) || (rc = tmp.get(&a.pos, n)) || (rc = tmp.get(&a.parent, n)) ||
+        (voff && (rc = tmp.get(&d_voff, k + 1)))) {
+        tmp.release_all();
+        return rc;
+    }
+    int32_t largest = n;
+    std::vector<int32_t> v32;
+    if (voff) {
+        v32.resize(k + 1);
+        largest = 0;
+        for (int32_t g = 0; g <= k; ++g) v32[g] = int32_t(voff[g]);
+        for (int32_t g = 0; g < k; ++g) largest = std::max(largest, v32[g + 1] - v32[g]);
+    }
+    a.row_ptr = rp;
+    a.col_idx = ci;
+    a.voff = d_voff;
+    a.k = voff ? k : 1;
+    a.n_total = n;
+    cudaError_t e = voff ? cudaMemcpyAsync(d_voff, v32.data(), 4 * size_t(k + 1), cudaMemcpyHostToDevice, s)
+                         : cudaSuccess;
+    if (!e) e = lms::launch_bfs(a, lms::bfs_cluster_size(largest), s);
+    if (!e) e = cudaMemcpyAsync(out, a.out, 4 * size_t(n), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    tmp.release_all();
+    if (e) {
+        lms::set_error_detail(std::string("device BFS: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    return LMS_OK;
+}
+
 // Move the mesh to storage order `perm_new` (new_to_old): CSR rows gathered from the original
 // ones with ids mapped, triangles mapped, boundary bits, positions carried over.
 int apply_layout(lms_mesh_s* h, const std::vector<int32_t>& perm_new) {
@@ -692,8 +734,14 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
         LMS_CUDA(cudaStreamSynchronize(h->stream));
     }
     std::vector<int32_t> p(h->n);
-    LMS_TRY(lms::order_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), q.empty() ? nullptr : q.data(),
-                                ordering, seed, p.data()));
+    if (ordering == LMS_BFS || ordering == LMS_RBFS) {
+        // level-synchronous search on the device, equal to the sequential one
+        LMS_TRY(device_bfs(h->arena.al, h->stream, h->d_rp0, h->d_ci0, h->n, 1, nullptr, p.data()));
+        if (ordering == LMS_RBFS) std::reverse(p.begin(), p.end());
+    } else {
+        LMS_TRY(lms::order_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), q.empty() ? nullptr : q.data(),
+                                    ordering, seed, p.data()));
+    }
     h->user_perm = p;
     h->colours_valid = false;
     h->coloured_layout = false;
@@ -1350,9 +1398,15 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
             return fail_orig(LMS_ERR_CUDA);
         }
     }
-    // per-mesh orderings on host threads
+    // per-mesh orderings: breadth-first ones on the device (one search per mesh), the others on
+    // host threads
     b->perm.resize(N);
-    {
+    if (ordering == LMS_BFS || ordering == LMS_RBFS) {
+        if ((rc = device_bfs(b->arena.al, s, d_rp0, d_ci0, N, k, b->voff.data(), b->perm.data())))
+            return fail_orig(rc);
+        if (ordering == LMS_RBFS)
+            for (int32_t m = 0; m < k; ++m) std::reverse(b->perm.begin() + b->voff[m], b->perm.begin() + b->voff[m + 1]);
+    } else {
         std::atomic<int32_t> next(0);
         unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         std::vector<std::thread> pool;

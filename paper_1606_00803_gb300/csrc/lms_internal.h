@@ -86,6 +86,22 @@ cudaError_t launch_sweep_staged(int precision, bool in_place, const StagedArgs& 
                                 cudaStream_t stream);
 int staged_occupancy(int precision, bool in_place, int block, int32_t tile_cap, int32_t e_cap);
 
+// Breadth-first orderings of k graphs on the device (k_bfs).  Graph g holds vertices
+// [voff[g], voff[g+1]) (voff NULL: one graph of n_total vertices) and its CSR uses global ids;
+// out[voff[g] + p] = global id at queue position p.  pos and parent are [n_total] scratch.
+struct BfsArgs {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const int32_t* voff;
+    int32_t k;
+    int32_t n_total;
+    int32_t* out;
+    int32_t* pos;
+    int32_t* parent;
+};
+int bfs_cluster_size(int32_t max_graph_vertices);
+cudaError_t launch_bfs(const BfsArgs& a, int cluster, cudaStream_t stream);
+
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
 // Batched FP32 sweep over a SELL-C-sigma work layout (see k_batch_sell).

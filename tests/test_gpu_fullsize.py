@@ -54,6 +54,15 @@ def test_workload1_fp32_jacobi_100(w1, ordering):
     assert np.abs(got - want).max() <= TOL32 * diag(m)
 
 
+@pytest.mark.parametrize("ordering", [lms.BFS, lms.RBFS])
+def test_workload1_device_bfs_orderings(w1, ordering):
+    want = oracle.order(w1, oracle.BFS)
+    with lms.Mesh.from_dict(w1, lms.FP32) as g:
+        g.reorder(ordering)
+        got = g.permutation()
+    assert np.array_equal(got, want if ordering == lms.BFS else want[::-1])
+
+
 @pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
 def test_workload1_coloured_gs_bfs(w1, precision):
     m = w1
@@ -121,3 +130,12 @@ def test_workload3_batched_full_size_sampled():
         assert np.array_equal(x[bd], m["xy"][bd])
         lo, hi = m["xy"].min(axis=0), m["xy"].max(axis=0)
         assert (x >= lo - 1e-6).all() and (x <= hi + 1e-6).all()
+
+
+def test_workload3_batch_device_bfs_sampled():
+    meshes = meshgen.batch_workload()
+    with lms.Batch(meshes, ordering=lms.BFS) as b:
+        sizes = [m["n"] for m in meshes]
+        for i in sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 0, 511, 77, 300}):
+            m = meshes[i]
+            assert np.array_equal(b.permutation(i), oracle.order_bfs(m["row_ptr"], m["col_idx"]))
