@@ -224,6 +224,11 @@ int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx, int32_t* stora
    device time in ms, Q before and after (NaN when no stopping rule ran).  Any pointer may be NULL. */
 int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, double* q_last);
 
+/* Wall time of the last lms_reorder in ms: computing the ordering (RDR: device quality keys + host
+   walk; BFS / reversed BFS: device search + copy of the permutation to the host; RANDOM: host shuffle)
+   and building the relabelled layout on the device.  NaN before the first lms_reorder.  [host] */
+int lms_last_reorder_ms(lms_handle h, double* ordering_ms, double* layout_ms);
+
 /* Free a handle and its device memory (NULL is ignored). */
 void lms_destroy(lms_handle h);
 

@@ -79,6 +79,7 @@ _SIGS = {
     "lms_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
     "lms_last_stats": ([_P, _PD, _PD, _PD, _PD], ctypes.c_int),
     "lms_last_launches": ([_P, _PI64], ctypes.c_int),
+    "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_batch_create": ([_I32, ctypes.POINTER(MeshDesc), ctypes.c_int, _U64, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -329,6 +330,12 @@ class Mesh:
         k = ctypes.c_int64()
         _check(_lib().lms_last_launches(self._handle(), ctypes.byref(k)), "lms_last_launches")
         return k.value
+
+    def last_reorder_ms(self):
+        """(ordering ms, relabelled-layout ms) of the last reorder."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(_lib().lms_last_reorder_ms(self._handle(), ctypes.byref(a), ctypes.byref(b)), "lms_last_reorder_ms")
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "_h", None) is not None:

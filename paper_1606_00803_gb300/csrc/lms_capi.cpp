@@ -269,6 +269,7 @@ struct lms_mesh_s {
     bool stats_pending = false;
     int last_disp_slot = 0;
     double last_disp = NAN, last_ms = NAN, q_first = NAN, q_last = NAN;
+    double reorder_ms[2] = {NAN, NAN};  // last lms_reorder: ordering, relabelled layout
 
     ~lms_mesh_s() {
         if (stream) cudaStreamSynchronize(stream);
@@ -720,6 +721,8 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     if (!h || ordering < LMS_ORI || ordering > LMS_RBFS) return LMS_ERR_ARG;
     if (ordering == LMS_RDR && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));  // earlier work does not count towards the ordering time
+    const auto t0 = std::chrono::steady_clock::now();
     std::vector<double> q;
     if (ordering == LMS_RDR) {
         // keys: Section 3.2 vertex qualities of the current positions, FP64, original labels
@@ -742,11 +745,24 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
         LMS_TRY(lms::order_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), q.empty() ? nullptr : q.data(),
                                     ordering, seed, p.data()));
     }
+    const auto t1 = std::chrono::steady_clock::now();
     h->user_perm = p;
     h->colours_valid = false;
     h->coloured_layout = false;
     LMS_TRY(apply_layout(h, p));
-    return build_items(h);
+    LMS_TRY(build_items(h));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));
+    const auto t2 = std::chrono::steady_clock::now();
+    h->reorder_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    h->reorder_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    return LMS_OK;
+}
+
+int lms_last_reorder_ms(lms_handle h, double* ordering_ms, double* layout_ms) {
+    if (!h) return LMS_ERR_ARG;
+    if (ordering_ms) *ordering_ms = h->reorder_ms[0];
+    if (layout_ms) *layout_ms = h->reorder_ms[1];
+    return LMS_OK;
 }
 
 int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile) {

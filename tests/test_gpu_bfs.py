@@ -63,3 +63,13 @@ def test_device_bfs_batch_of_many_meshes():
     with lms.Batch(meshes, ordering=lms.BFS) as b:
         for i, m in enumerate(meshes):
             assert np.array_equal(b.permutation(i), oracle.order_bfs(m["row_ptr"], m["col_idx"]))
+
+
+def test_reorder_times_are_reported():
+    m = meshgen.workload(1, side=50)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        assert all(np.isnan(t) for t in g.last_reorder_ms())
+        for o in (lms.BFS, lms.RDR, lms.RANDOM, lms.ORI, lms.RBFS):
+            g.reorder(o)
+            order_ms, layout_ms = g.last_reorder_ms()
+            assert 0.0 <= order_ms < 60e3 and 0.0 <= layout_ms < 60e3
