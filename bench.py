@@ -463,16 +463,32 @@ def run_ours(args, dist):
     b.close()
 
 
+def _braced_block(text, start):
+    """text[start:] up to the brace that closes the first opening brace after start."""
+    i = text.index("{", start)
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return text[start:j + 1]
+    raise ValueError("unbalanced braces")
+
+
 def kernel_source_digest():
-    """sha256 over the library's device sources: any change makes recorded counters stale."""
+    """sha256 over the source of the batched sweep kernel (k_batch_sweep), its argument struct and the
+    device helpers it calls: any change to them makes recorded counters stale."""
     import hashlib
-    h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1606_00803_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if not name.endswith((".cu", ".cuh")) and name != "lms_internal.h":
-            continue  # host-only sources do not change what a kernel moves
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+    kernels = open(os.path.join(csrc, "lms_kernels.cu")).read()
+    internal = open(os.path.join(csrc, "lms_internal.h")).read()
+    parts = [
+        _braced_block(kernels, kernels.index("template <int CHUNK, bool EXTRAS>\n__global__ void __launch_bounds__(512) k_batch_sweep")),
+        _braced_block(internal, internal.index("struct SweepArgs {")),
+        open(os.path.join(csrc, "lms_device.cuh")).read(),
+    ]
+    h = hashlib.sha256()
+    for p in parts:
+        h.update(p.encode() + b"\0")
     return h.hexdigest()
 
 
