@@ -74,6 +74,11 @@ extern "C" {
 #define LMS_COLORED_GS 1 /* in place, colour by colour of a first-fit colouring of the interior vertices
                             in storage order; equals Algorithm 1's sequential in-place sweep taken in
                             (colour, storage position) order */
+#define LMS_INPLACE_STATIC 2 /* the paper's parallel form (Section 5.1): Algorithm 1 in place with the
+                                storage order divided evenly into contiguous blocks, one GPU thread per
+                                block (lms_set_inplace_split); neighbours are read as they are at that
+                                moment, so results depend on timing - except with one thread, which is
+                                the sequential in-place sweep in storage order */
 
 /* sweep kernels */
 #define LMS_KERNEL_DIRECT 0 /* one thread per vertex; CSR and positions loaded through L1; rows read `chunk`
@@ -223,6 +228,10 @@ int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx, int32_t* stora
 /* Statistics of the last lms_smooth: largest vertex displacement of its final sweep (original units),
    device time in ms, Q before and after (NaN when no stopping rule ran).  Any pointer may be NULL. */
 int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, double* q_last);
+
+/* Number of GPU threads (contiguous blocks of the storage order) of LMS_INPLACE_STATIC sweeps; 0 = one
+   per resident thread slot of the device (the default), 1 = the sequential Algorithm 1.  [host] */
+int lms_set_inplace_split(lms_handle h, int32_t threads);
 
 /* Wall time of the last lms_reorder in ms: computing the ordering (RDR: device quality keys + host
    walk; BFS / reversed BFS: device search + copy of the permutation to the host; RANDOM: host shuffle)

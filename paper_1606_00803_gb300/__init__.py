@@ -24,10 +24,10 @@ from . import _build
 FP64, FP32 = 0, 1
 KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
 ORI, RANDOM, BFS, RDR, RBFS = 0, 1, 2, 3, 4
-JACOBI, COLORED_GS = 0, 1
+JACOBI, COLORED_GS, INPLACE_STATIC = 0, 1, 2
 REUSE_DISTINCT, REUSE_ACCESSES = 0, 1
 ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS}
-MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS}
+MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS, "inplace_static": INPLACE_STATIC}
 PRECISIONS = {"fp64": FP64, "fp32": FP32}
 
 LMS_OK = 0
@@ -80,6 +80,7 @@ _SIGS = {
     "lms_last_stats": ([_P, _PD, _PD, _PD, _PD], ctypes.c_int),
     "lms_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
+    "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_batch_create": ([_I32, ctypes.POINTER(MeshDesc), ctypes.c_int, _U64, _P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -330,6 +331,10 @@ class Mesh:
         k = ctypes.c_int64()
         _check(_lib().lms_last_launches(self._handle(), ctypes.byref(k)), "lms_last_launches")
         return k.value
+
+    def set_inplace_split(self, threads):
+        """GPU threads of INPLACE_STATIC sweeps (0 = default, 1 = sequential Algorithm 1)."""
+        _check(_lib().lms_set_inplace_split(self._handle(), int(threads)), "lms_set_inplace_split")
 
     def last_reorder_ms(self):
         """(ordering ms, relabelled-layout ms) of the last reorder."""

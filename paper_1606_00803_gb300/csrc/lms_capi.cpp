@@ -270,6 +270,7 @@ struct lms_mesh_s {
     int last_disp_slot = 0;
     double last_disp = NAN, last_ms = NAN, q_first = NAN, q_last = NAN;
     double reorder_ms[2] = {NAN, NAN};  // last lms_reorder: ordering, relabelled layout
+    int32_t inplace_threads = 0;        // LMS_INPLACE_STATIC split (0: one thread per resident slot)
 
     ~lms_mesh_s() {
         if (stream) cudaStreamSynchronize(stream);
@@ -419,7 +420,7 @@ int ensure_queue(lms_mesh_s* h, int32_t slots) {
     return LMS_OK;
 }
 
-int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_JACOBI ? 1 : h->ncolours; }
+int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_COLORED_GS ? h->ncolours : 1; }
 
 // FP32 Jacobi with the direct kernel runs on the work-queue sweep (rows in chunks of 4).
 bool uses_queue_sweep(const lms_mesh_s* h, int mode) {
@@ -444,6 +445,14 @@ int ensure_colours(lms_mesh_s* h) {
                                  h->colour.data(), &h->ncolours));
     h->colours_valid = true;
     return LMS_OK;
+}
+
+// The ordering's own layout (after a coloured Gauss-Seidel moved the mesh to the colour-major one).
+int ensure_ordering_layout(lms_mesh_s* h) {
+    if (!h->coloured_layout) return LMS_OK;
+    LMS_TRY(apply_layout(h, h->user_perm));
+    h->coloured_layout = false;
+    return build_items(h);
 }
 
 int ensure_coloured_layout(lms_mesh_s* h) {
@@ -487,6 +496,13 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
 // base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
 int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
     const int src = (base + k1 - 1) & 1;
+    if (mode == LMS_INPLACE_STATIC) {
+        SweepArgs a = sweep_args(h, base, base);
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        const int32_t threads = h->inplace_threads > 0 ? h->inplace_threads : std::min(h->n, h->sms * 2048);
+        return check_launch(lms::launch_inplace_static(h->precision, a, threads, s), "inplace_static");
+    }
     if (h->kernel == LMS_KERNEL_STAGED) {
         lms::StagedArgs a{};
         a.row_ptr = h->d_rp;
@@ -758,6 +774,14 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     return LMS_OK;
 }
 
+int lms_set_inplace_split(lms_handle h, int32_t threads) {
+    if (!h || threads < 0) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    h->inplace_threads = threads;
+    h->graphs.clear();
+    return LMS_OK;
+}
+
 int lms_last_reorder_ms(lms_handle h, double* ordering_ms, double* layout_ms) {
     if (!h) return LMS_ERR_ARG;
     if (ordering_ms) *ordering_ms = h->reorder_ms[0];
@@ -790,10 +814,13 @@ int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile) {
 }
 
 int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done) {
-    if (!h || max_iters < 0 || (mode != LMS_JACOBI && mode != LMS_COLORED_GS) || std::isnan(tol)) return LMS_ERR_ARG;
+    if (!h || max_iters < 0 || (mode != LMS_JACOBI && mode != LMS_COLORED_GS && mode != LMS_INPLACE_STATIC) ||
+        std::isnan(tol))
+        return LMS_ERR_ARG;
     if (tol >= 0.0 && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
     if (mode == LMS_COLORED_GS) LMS_TRY(ensure_coloured_layout(h));
+    if (mode == LMS_INPLACE_STATIC) LMS_TRY(ensure_ordering_layout(h));
     if (iters_done) *iters_done = 0;
     h->q_first = h->q_last = NAN;
     h->last_disp = NAN;

@@ -104,6 +104,9 @@ cudaError_t launch_bfs(const BfsArgs& a, int cluster, cudaStream_t stream);
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
+// The paper's static-schedule in-place sweep over [0, a.v_end) split into `threads` contiguous blocks
+// (k_inplace_static); positions in a.dst, updated in place.
+cudaError_t launch_inplace_static(int precision, const SweepArgs& a, int32_t threads, cudaStream_t stream);
 // Batched FP32 sweep over a SELL-C-sigma work layout (see k_batch_sell).
 struct SellArgs {
     const int32_t* col;            // column-major neighbour ids per slice, -1 past a slot's row

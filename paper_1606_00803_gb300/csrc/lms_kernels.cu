@@ -109,6 +109,61 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (want) record_disp(a.disp2, d2);
 }
 
+// The paper's parallel in-place sweep (Section 5.1: Algorithm 1 under a static schedule that divides the
+// vertices evenly between threads): thread t sweeps storage positions [t * per_thread, (t + 1) *
+// per_thread) in order, in place, reading each neighbour as it is at that moment - possibly already
+// moved by another thread in this sweep.  Neighbour loads and the store go through L2 (ld/st.global.cg)
+// so a thread sees other threads' updates as soon as they land there, not a stale L1 copy.  With one
+// thread this is the sequential Algorithm 1 in storage order; otherwise the result depends on timing.
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_inplace_static(SweepArgs a, int32_t per_thread) {
+    if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
+    using V = typename std::conditional<FP64, double2, float2>::type;
+    __shared__ double s_recip[kMaxRecipDeg + 1];
+    if (FP64) {
+        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
+        __syncthreads();
+    }
+    V* pos = static_cast<V*>(a.dst);
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t lo = min(t * per_thread, static_cast<int64_t>(a.v_end));
+    const int64_t hi = min(lo + per_thread, static_cast<int64_t>(a.v_end));
+    const bool want = a.disp2 != nullptr;
+    double dmax = 0.0;
+    for (int32_t v = static_cast<int32_t>(lo); v < hi; ++v) {
+        if (boundary_bit(a.bnd_bits, v)) continue;
+        const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+        V r;
+        if constexpr (FP64) {
+            double sx = 0.0, sy = 0.0;
+            for (int32_t e = e0; e < e1; ++e) {
+                const V p = __ldcg(pos + __ldg(a.col_idx + e));
+                sx = __dadd_rn(sx, p.x);
+                sy = __dadd_rn(sy, p.y);
+            }
+            r.x = div_by_count(sx, e1 - e0, s_recip);
+            r.y = div_by_count(sy, e1 - e0, s_recip);
+        } else {
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int32_t e = e0; e < e1; ++e) {
+                const V p = __ldcg(pos + __ldg(a.col_idx + e));
+                kahan_add(sx, cx, p.x);
+                kahan_add(sy, cy, p.y);
+            }
+            r.x = mean_f32(sx, cx, e1 - e0);
+            r.y = mean_f32(sy, cy, e1 - e0);
+        }
+        if (want) {
+            const V o = __ldcg(pos + v);
+            const double ex = static_cast<double>(r.x) - static_cast<double>(o.x);
+            const double ey = static_cast<double>(r.y) - static_cast<double>(o.y);
+            dmax = fmax(dmax, __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+        }
+        __stcg(pos + v, r);
+    }
+    if (want) record_disp(a.disp2, dmax);
+}
+
 // Batched FP32 Jacobi: a persistent grid pulls vertex tiles (never crossing a mesh) from a device counter;
 // the next tile is requested while the current one is processed.  One thread per vertex; a row is read
 // CHUNK entries at a time - all neighbour ids, then all position gathers, then the Kahan sums in row
@@ -583,6 +638,17 @@ cudaError_t launch_stop_check(const double* partials, double n, DevState* state,
 cudaError_t launch_gather_rows(int32_t n, const int32_t* new_to_old, const int32_t* rp_src, const int32_t* ci_src,
                                const int32_t* rp_dst, int32_t* ci_dst, const int32_t* map, cudaStream_t stream) {
     k_gather_rows<<<blocks_for(n, 256), 256, 0, stream>>>(n, new_to_old, rp_src, ci_src, rp_dst, ci_dst, map);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inplace_static(int precision, const SweepArgs& a, int32_t threads, cudaStream_t stream) {
+    if (threads <= 0 || a.v_end <= 0) return cudaErrorInvalidValue;
+    const int32_t per = static_cast<int32_t>((static_cast<int64_t>(a.v_end) + threads - 1) / threads);
+    const int blocks = static_cast<int>((static_cast<int64_t>(threads) + 255) / 256);
+    if (precision == LMS_FP64)
+        k_inplace_static<true><<<blocks, 256, 0, stream>>>(a, per);
+    else
+        k_inplace_static<false><<<blocks, 256, 0, stream>>>(a, per);
     return cudaGetLastError();
 }
 
