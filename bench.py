@@ -220,6 +220,36 @@ def cpu_rate_oracle(meshes, sweeps, budget_s):
     return updates / spent, dict(meshes=used, vertices=verts, sweeps=sweeps, seconds=spent)
 
 
+def cpu_orderings_oracle():
+    """The paper's serial experiment on the host: the 1024 x 1024 mesh stored under each ordering (CSR rows
+    and positions relabelled by the oracle), then one oracle in-place sweep in storage order (Algorithm 1,
+    the paper's serial method) and one oracle Jacobi sweep, single thread, best of 3."""
+    import numpy as np
+    import meshgen
+    import oracle
+    m = meshgen.workload(1)
+    n_int = int((m["is_boundary"] == 0).sum())
+    out = {}
+    for name, o in ORDERINGS:
+        p = oracle.order(m, o, seed=meshgen.BASE_SEED + 7)
+        rp, ci = oracle.relabel(m["row_ptr"], m["col_idx"], p)
+        xy, bnd = np.ascontiguousarray(m["xy"][p]), np.ascontiguousarray(m["is_boundary"][p])
+        seq = np.arange(m["n"], dtype=np.int32)
+        best = {}
+        for kind, fn in (("inplace", lambda: oracle.inplace_sweep(rp, ci, bnd, seq, xy)),
+                         ("jacobi", lambda: oracle.jacobi_sweep(rp, ci, bnd, xy))):
+            ts = []
+            for _ in range(3):
+                t = time.perf_counter()
+                fn()
+                ts.append(time.perf_counter() - t)
+            best[kind] = min(ts)
+        out[name] = dict(inplace_ms=round(best["inplace"] * 1e3, 2), jacobi_ms=round(best["jacobi"] * 1e3, 2),
+                         inplace_updates_per_s=n_int / best["inplace"])
+    return dict(workload="1024 x 1024 mesh (%d vertices) stored under each ordering; one sweep, oracle, 1 thread, "
+                         "best of 3 (sweep time includes copying the 18 MB position array)" % m["n"], rows=out)
+
+
 # ------------------------------------------------------------------ our arm
 
 
@@ -460,6 +490,8 @@ def run_ours(args, dist):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "first %d of the %d meshes (%d vertices), %d Jacobi sweeps each, FP64, one thread, %.1f s"
                          % (sample["meshes"], k, sample["vertices"], sample["sweeps"], sample["seconds"])}
+        if not args.skip_extras:
+            cpu["per_ordering"] = cpu_orderings_oracle()
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
