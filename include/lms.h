@@ -297,6 +297,19 @@ int lms_batch_get_all_coords(lms_batch b, double* xy);
    lms_batch_get_coords / lms_batch_get_all_coords. */
 int lms_batch_set_all_coords(lms_batch b, const double* xy);
 
+/*
+ * End-to-end batched smoothing from and to host memory: xy_in ([2 * n_total] FP64, the meshes'
+ * original orders concatenated, as for lms_batch_set_all_coords) -> `iters` Jacobi sweeps -> xy_out
+ * (same layout, as lms_batch_get_all_coords).  The meshes are split into `groups` runs of whole meshes
+ * with about equal vertex counts; each group's input copy, sweeps and output copy are ordered, and the
+ * copies of one group overlap the sweeps of the others (two copy streams, one compute stream).  The
+ * result equals lms_batch_set_all_coords + lms_batch_smooth(iters) + lms_batch_get_all_coords bit for
+ * bit, and afterwards the batch holds it as after those calls.  The copies overlap only when xy_in and
+ * xy_out are page-locked.  groups in [1, k] (the SELL kernel always uses 1).  Synchronous.  Returns
+ * LMS_ERR_ARG (NULL, bad counts, or a non-finite input value), LMS_ERR_CUDA.
+ */
+int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iters, int32_t groups);
+
 /* Totals: vertices, interior vertices, CSR entries, tiles (any pointer may be NULL). [no device work] */
 int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles);
 

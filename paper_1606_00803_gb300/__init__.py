@@ -88,6 +88,7 @@ _SIGS = {
     "lms_batch_get_coords": ([_P, _I32, _P], ctypes.c_int),
     "lms_batch_get_all_coords": ([_P, _P], ctypes.c_int),
     "lms_batch_set_all_coords": ([_P, _P], ctypes.c_int),
+    "lms_batch_run": ([_P, _P, _P, _I32, _I32], ctypes.c_int),
     "lms_batch_info": ([_P, _PI64, _PI64, _PI64, _PI32], ctypes.c_int),
     "lms_batch_get_config": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
     "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
@@ -409,6 +410,17 @@ class Batch:
         xy = _host_f64(xy, self.n_total)
         _check(_lib().lms_batch_set_all_coords(self._handle(), _ptr(xy)), "lms_batch_set_all_coords")
         self._pending = xy
+
+    def run(self, xy_in, iters, groups=4, out=None):
+        """lms_batch_run: positions in (host), iters sweeps, positions out (host), pipelined over groups of
+        meshes.  xy_in / out: contiguous FP64 host arrays or page-locked torch tensors of 2 * n_total values."""
+        xy_in = _host_f64(xy_in, self.n_total)
+        if out is None:
+            out = np.empty((self.n_total, 2), np.float64)
+        else:
+            out = _host_f64(out, self.n_total)
+        _check(_lib().lms_batch_run(self._handle(), _ptr(xy_in), _ptr(out), int(iters), int(groups)), "lms_batch_run")
+        return out
 
     def permutation(self, mesh):
         p = np.empty(self.sizes[mesh], np.int32)

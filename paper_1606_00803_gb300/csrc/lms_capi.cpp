@@ -1086,11 +1086,22 @@ struct lms_batch_s {
     GraphCache graphs;
     int64_t last_launches = 0;
     int sms = 0;
+    // lms_batch_run: copy streams and per-group events
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_done;
+    cudaEvent_t ev_start = nullptr;
 
     ~lms_batch_s() {
         if (stream) cudaStreamSynchronize(stream);
+        if (s_in) cudaStreamSynchronize(s_in);
+        if (s_out) cudaStreamSynchronize(s_out);
         graphs.clear();
         arena.release_all();
+        for (cudaEvent_t e : ev_in) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_done) cudaEventDestroy(e);
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_out) cudaStreamDestroy(s_out);
         if (cap) cudaStreamDestroy(cap);
     }
 };
@@ -1233,6 +1244,21 @@ int batch_occupancy(lms_batch_s* b) {
 }
 
 // one sweep of the batch on stream s: reads buffer src, writes dst, counts tiles in queue slot `slot`
+// one sweep over the tiles [i0, i1) of the item table (direct and staged kernels; meshes never share a
+// tile, so a range of tiles is a range of whole meshes when it starts and ends at mesh boundaries)
+int batch_issue_range(lms_batch_s* b, int src, int dst, int slot, int grid, cudaStream_t s, int32_t i0, int32_t i1) {
+    if (b->kernel == LMS_KERNEL_STAGED) {
+        lms::StagedArgs a = batch_staged_args(b, src, dst, slot);
+        a.items += i0;
+        a.n_items = i1 - i0;
+        return check_launch(lms::launch_sweep_staged(LMS_FP32, false, a, grid, b->block, s), "staged_sweep");
+    }
+    SweepArgs a = batch_args(b, src, dst, slot);
+    a.items += i0;
+    a.n_items = i1 - i0;
+    return check_launch(lms::launch_batch_sweep(a, b->block, b->chunk, grid, s), "batch_sweep");
+}
+
 int batch_issue(lms_batch_s* b, int src, int dst, int slot, int grid, cudaStream_t s) {
     if (b->kernel == LMS_KERNEL_SELL) {
         lms::SellArgs a{};
@@ -1699,6 +1725,103 @@ int lms_batch_set_all_coords(lms_batch b, const double* xy) {
                          "batch_load_xy"));
     b->cur = 0;
     return LMS_OK;
+}
+
+int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iters, int32_t groups) {
+    if (!b || !xy_in || !xy_out || iters < 0 || groups < 1 || groups > b->k) return LMS_ERR_ARG;
+    if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr, nullptr));
+    if (b->kernel == LMS_KERNEL_SELL) groups = 1;  // SELL tiles are not ordered by mesh
+    cudaStream_t s = b->stream;
+    if (!b->s_in) {
+        LMS_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
+        LMS_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+        LMS_CUDA(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
+    }
+    while (int32_t(b->ev_in.size()) < groups) {
+        cudaEvent_t e0, e1;
+        LMS_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+        LMS_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+        b->ev_in.push_back(e0);
+        b->ev_done.push_back(e1);
+    }
+    // groups of whole meshes with about equal vertex counts, as tile ranges [it[g], it[g+1]) and vertex
+    // ranges [vt[g], vt[g+1])
+    std::vector<int32_t> it(groups + 1, b->n_items);
+    std::vector<int64_t> vt(groups + 1, b->n_total);
+    {
+        std::vector<int32_t> first_tile(b->k + 1, 0);
+        const int tile = b->items_tile;
+        for (int32_t m = 0; m < b->k; ++m)
+            first_tile[m + 1] = first_tile[m] + int32_t((b->voff[m + 1] - b->voff[m] + tile - 1) / tile);
+        // group g starts at mesh mb: the first mesh at or past g/groups of the vertices, keeping at least
+        // one mesh for each group
+        int32_t mb = 0;
+        for (int32_t g = 0; g < groups; ++g) {
+            if (g > 0) {
+                const int64_t goal = b->n_total * g / groups;
+                ++mb;
+                while (mb < b->k - (groups - g) && b->voff[mb] < goal) ++mb;
+            }
+            it[g] = first_tile[mb];
+            vt[g] = b->voff[mb];
+        }
+    }
+    const int32_t slots = groups * std::max(iters, 1);
+    LMS_TRY(ensure_queue(b, slots));
+    const int grid = batch_grid(b);
+    const int fin = iters & 1;
+    // earlier work on the caller's stream (which may read d_fixed) comes first
+    LMS_CUDA(cudaEventRecord(b->ev_start, s));
+    LMS_CUDA(cudaStreamWaitEvent(b->s_in, b->ev_start, 0));
+    LMS_CUDA(cudaMemsetAsync(b->d_err + 1, 0, sizeof(int32_t), s));
+    for (int32_t g = 0; g < groups; ++g) {
+        const int64_t v0 = vt[g], nv = vt[g + 1] - vt[g];
+        LMS_CUDA(cudaMemcpyAsync(b->d_fixed + 2 * v0, xy_in + 2 * v0, 16 * size_t(nv), cudaMemcpyHostToDevice, b->s_in));
+        LMS_CUDA(cudaEventRecord(b->ev_in[g], b->s_in));
+    }
+    int64_t kernels_total = 0;
+    for (int32_t g = 0; g < groups; ++g) {
+        const int32_t i0 = it[g], i1 = it[g + 1];
+        const std::string key = "run/" + std::to_string(g) + "/" + std::to_string(groups) + "/" + std::to_string(iters);
+        cudaGraphExec_t exec;
+        int64_t kernels = 0;
+        auto found = b->graphs.execs.find(key);
+        if (found != b->graphs.execs.end()) {
+            exec = found->second;
+            kernels = b->graphs.kernels[key];
+        } else {
+            LMS_TRY(capture(
+                b->cap,
+                [&](cudaStream_t cs) -> int {
+                    const int32_t q0 = g * std::max(iters, 1);
+                    LMS_CUDA(cudaMemsetAsync(b->d_queue + q0, 0, sizeof(int32_t) * std::max(iters, 1), cs));
+                    LMS_TRY(check_launch(lms::launch_batch_load_xy(i1 - i0, b->d_items + i0, b->d_item_mesh + i0,
+                                                                   b->d_perm, b->d_fixed, b->d_xy[0], b->d_xy[1],
+                                                                   b->d_cs, b->d_err + 1, cs),
+                                         "batch_load_xy"));
+                    for (int32_t k = 0; k < iters; ++k)
+                        LMS_TRY(batch_issue_range(b, k & 1, (k & 1) ^ 1, q0 + k, grid, cs, i0, i1));
+                    return check_launch(lms::launch_batch_store_xy(i1 - i0, b->d_items + i0, b->d_item_mesh + i0,
+                                                                   b->d_perm, b->d_xy[fin], b->d_xy64, b->d_cs,
+                                                                   b->d_bits, b->d_fixed, cs),
+                                        "batch_store_xy");
+                },
+                &exec, &kernels));
+            b->graphs.execs[key] = exec;
+            b->graphs.kernels[key] = kernels;
+        }
+        LMS_CUDA(cudaStreamWaitEvent(s, b->ev_in[g], 0));
+        LMS_CUDA(cudaGraphLaunch(exec, s));
+        LMS_CUDA(cudaEventRecord(b->ev_done[g], s));
+        LMS_CUDA(cudaStreamWaitEvent(b->s_out, b->ev_done[g], 0));
+        const int64_t v0 = vt[g], nv = vt[g + 1] - vt[g];
+        LMS_CUDA(cudaMemcpyAsync(xy_out + 2 * v0, b->d_xy64 + 2 * v0, 16 * size_t(nv), cudaMemcpyDeviceToHost, b->s_out));
+        kernels_total += kernels;
+    }
+    LMS_CUDA(cudaStreamSynchronize(b->s_out));
+    b->last_launches = kernels_total;
+    b->cur = fin;
+    return batch_check_err(b);
 }
 
 int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* nnz_total, int32_t* n_tiles) {

@@ -388,3 +388,36 @@ def test_batched_rejects_non_finite_coordinates_on_next_read():
         b.set_all_coords(xy)
         b.smooth(3)
         assert np.isfinite(b.all_coords()).all()
+
+
+@pytest.mark.parametrize("groups", [1, 3, 10])
+def test_batched_run_equals_set_smooth_get(groups):
+    meshes = small_batch(10)
+    xy = np.concatenate([m["xy"] for m in meshes])
+    with lms.Batch(meshes, ordering=lms.RDR) as b:
+        b.set_config(lms.KERNEL_DIRECT, 128, 4, 256)
+        b.set_all_coords(xy)
+        b.smooth(17)
+        want = b.all_coords()
+        b.smooth(3)  # move away, then start over from xy
+        got = b.run(xy, 17, groups=groups)
+        assert np.array_equal(got, want)
+        assert np.array_equal(b.all_coords(), want)  # the batch holds the result afterwards
+        assert np.array_equal(b.run(xy, 0, groups=groups), b.run(xy, 0, groups=1))
+    for i, m in enumerate(meshes):
+        o = sum(x["n"] for x in meshes[:i])
+        w, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 17)
+        assert err(got[o:o + m["n"]], w, m) <= TOL32
+
+
+def test_batched_run_rejects_bad_input():
+    meshes = small_batch(3)
+    xy = np.concatenate([m["xy"] for m in meshes])
+    with lms.Batch(meshes, ordering=lms.BFS) as b:
+        with pytest.raises(lms.LmsError):
+            b.run(xy, 5, groups=4)  # more groups than meshes
+        bad = xy.copy()
+        bad[7, 1] = np.nan
+        with pytest.raises(lms.LmsError):
+            b.run(bad, 5, groups=2)
+        assert np.isfinite(b.run(xy, 5, groups=2)).all()
