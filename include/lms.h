@@ -301,8 +301,9 @@ int lms_batch_set_all_coords(lms_batch b, const double* xy);
  * End-to-end batched smoothing from and to host memory: xy_in ([2 * n_total] FP64, the meshes'
  * original orders concatenated, as for lms_batch_set_all_coords) -> `iters` Jacobi sweeps -> xy_out
  * (same layout, as lms_batch_get_all_coords).  The meshes are split into `groups` runs of whole meshes
- * with about equal vertex counts; each group's input copy, sweeps and output copy are ordered, and the
- * copies of one group overlap the sweeps of the others (two copy streams, one compute stream).  The
+ * whose vertex counts ramp up and down by a factor of 4 (1 : 4 : 16 : ... : 4 : 1); each group's input
+ * copy, sweeps and output copy are ordered, and the copies of one group overlap the sweeps of the others
+ * (two copy streams, one compute stream), so only the first input and the last output copy are exposed.  The
  * result equals lms_batch_set_all_coords + lms_batch_smooth(iters) + lms_batch_get_all_coords bit for
  * bit, and afterwards the batch holds it as after those calls.  The copies overlap only when xy_in and
  * xy_out are page-locked.  groups in [1, k] (the SELL kernel always uses 1).  Synchronous.  Returns

@@ -1753,12 +1753,18 @@ int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iter
         const int tile = b->items_tile;
         for (int32_t m = 0; m < b->k; ++m)
             first_tile[m + 1] = first_tile[m] + int32_t((b->voff[m + 1] - b->voff[m] + tile - 1) / tile);
-        // group g starts at mesh mb: the first mesh at or past g/groups of the vertices, keeping at least
-        // one mesh for each group
+        // Group sizes ramp up and down by a factor of 4 (1, 4, 16, ..., 16, 4, 1): only the first
+        // group's input copy and the last group's output copy are exposed, and every other copy hides
+        // behind the sweeps of a neighbouring group at least a quarter of its size (a sweep pass over
+        // a vertex takes several times longer than copying it).  Group g starts at the first mesh at or
+        // past its share of the vertices, keeping at least one mesh for each group.
+        std::vector<double> cum(groups + 1, 0.0);
+        for (int32_t g = 0; g < groups; ++g)
+            cum[g + 1] = cum[g] + std::pow(4.0, double(std::min(g, groups - 1 - g)));
         int32_t mb = 0;
         for (int32_t g = 0; g < groups; ++g) {
             if (g > 0) {
-                const int64_t goal = b->n_total * g / groups;
+                const int64_t goal = int64_t(double(b->n_total) * cum[g] / cum[groups]);
                 ++mb;
                 while (mb < b->k - (groups - g) && b->voff[mb] < goal) ++mb;
             }
