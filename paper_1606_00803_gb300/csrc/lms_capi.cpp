@@ -256,9 +256,10 @@ struct lms_mesh_s {
     std::vector<int32_t> item_col_ofs;  // colour c: tiles [n_items_all + ofs[c], n_items_all + ofs[c+1])
     int32_t e_cap = 0;
     int32_t* d_rpf = nullptr;           // row offsets of the current layout with the boundary flag in bit 31
-    int2* d_items2 = nullptr;           // FP32 Jacobi work-queue tiles over [0, n)
+    int2* d_items2 = nullptr;           // FP32 work-queue tiles over [0, n), then over each colour's range
     int64_t items2_cap = 0;
-    int32_t n_items2 = 0;
+    int32_t n_items2 = 0;               // tiles over [0, n)
+    std::vector<int32_t> item2_col_ofs; // colour c: tiles [n_items2 + ofs[c], n_items2 + ofs[c+1])
     int32_t* d_queue = nullptr;         // one tile counter per work-queue launch of a graph
     int32_t queue_slots = 0;
     int32_t slot_next = 0;              // next counter while a graph is recorded
@@ -395,6 +396,14 @@ int build_items(lms_mesh_s* h) {
     constexpr int32_t kQueueTile = 512;
     std::vector<int2> items2;
     for (int32_t v = 0; v < h->n; v += kQueueTile) items2.push_back(make_int2(v, std::min(h->n, v + kQueueTile)));
+    const int32_t n_all2 = int32_t(items2.size());
+    h->item2_col_ofs.assign(1, 0);
+    if (h->coloured_layout)
+        for (int32_t c = 0; c < h->ncolours; ++c) {
+            for (int32_t v = h->colour_ofs[c]; v < h->colour_ofs[c + 1]; v += kQueueTile)
+                items2.push_back(make_int2(v, std::min(h->colour_ofs[c + 1], v + kQueueTile)));
+            h->item2_col_ofs.push_back(int32_t(items2.size()) - n_all2);
+        }
     if (int64_t(items2.size()) > h->items2_cap) {
         const int64_t cap = int64_t(items2.size()) + 16;
         LMS_TRY(h->arena.get(&h->d_items2, cap));
@@ -402,7 +411,7 @@ int build_items(lms_mesh_s* h) {
     }
     LMS_CUDA(cudaMemcpyAsync(h->d_items2, items2.data(), sizeof(int2) * items2.size(), cudaMemcpyHostToDevice,
                              h->stream));
-    h->n_items2 = int32_t(items2.size());
+    h->n_items2 = n_all2;
     LMS_CUDA(cudaMemcpyAsync(h->d_rpf, h->d_rp, sizeof(int32_t) * size_t(h->n + 1), cudaMemcpyDeviceToDevice,
                              h->stream));
     LMS_TRY(check_launch(lms::launch_flag_boundary_rows(h->n, h->d_bits, h->d_rpf, h->stream), "flag_rows"));
@@ -422,9 +431,9 @@ int ensure_queue(lms_mesh_s* h, int32_t slots) {
 
 int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_COLORED_GS ? h->ncolours : 1; }
 
-// FP32 Jacobi with the direct kernel runs on the work-queue sweep (rows in chunks of 4).
+// FP32 Jacobi and coloured GS with the direct kernel run on the work-queue sweep (rows in chunks of 4).
 bool uses_queue_sweep(const lms_mesh_s* h, int mode) {
-    return h->kernel == LMS_KERNEL_DIRECT && h->precision == LMS_FP32 && mode == LMS_JACOBI;
+    return h->kernel == LMS_KERNEL_DIRECT && h->precision == LMS_FP32 && (mode == LMS_JACOBI || mode == LMS_COLORED_GS);
 }
 
 // Current positions as FP64 in the original labelling, in d_xy64.
@@ -539,17 +548,29 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
     }
     if (uses_queue_sweep(h, mode)) {
         constexpr int kChunk = 4, kBlock = 128;
-        SweepArgs a = sweep_args(h, src, src ^ 1);
-        a.row_ptr = h->d_rpf;
-        a.items = h->d_items2;
-        a.n_items = h->n_items2;
-        if (h->slot_next >= h->queue_slots) return LMS_ERR_STATE;
-        a.queue = h->d_queue + h->slot_next++;
-        a.state = stoppable ? h->d_state : nullptr;
-        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
         const int occ = std::max(1, lms::batch_sweep_occupancy(kBlock, kChunk));
-        const int grid = std::max(1, std::min(occ * h->sms, a.n_items));
-        return check_launch(lms::launch_batch_sweep(a, kBlock, kChunk, grid, s), "queue_sweep");
+        // Jacobi: one launch over [0, n) from one buffer into the other.  Coloured GS: one launch per
+        // colour range, in place - a colour's vertices are never neighbours of one another, so no launch
+        // reads a position it writes.
+        const int ranges = mode == LMS_JACOBI ? 1 : h->ncolours;
+        for (int32_t c = 0; c < ranges; ++c) {
+            SweepArgs a = mode == LMS_JACOBI ? sweep_args(h, src, src ^ 1) : sweep_args(h, base, base);
+            a.row_ptr = h->d_rpf;
+            if (mode == LMS_JACOBI) {
+                a.items = h->d_items2;
+                a.n_items = h->n_items2;
+            } else {
+                a.items = h->d_items2 + h->n_items2 + h->item2_col_ofs[c];
+                a.n_items = h->item2_col_ofs[c + 1] - h->item2_col_ofs[c];
+            }
+            if (h->slot_next >= h->queue_slots) return LMS_ERR_STATE;
+            a.queue = h->d_queue + h->slot_next++;
+            a.state = stoppable ? h->d_state : nullptr;
+            a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+            const int grid = std::max(1, std::min(occ * h->sms, a.n_items));
+            LMS_TRY(check_launch(lms::launch_batch_sweep(a, kBlock, kChunk, grid, s), "queue_sweep"));
+        }
+        return LMS_OK;
     }
     if (mode == LMS_JACOBI) {
         SweepArgs a = sweep_args(h, src, src ^ 1);
