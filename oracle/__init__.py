@@ -14,6 +14,8 @@ Laplacian Mesh Smoothing"):
   relabel, color_greedy, color_sequence  storage under an ordering; the
                                   in-place order a coloured Gauss-Seidel follows
   order_rbfs                      reversed BFS (Section 2, Munson and Hovland)
+  order_brdr                      block RDR: Algorithm 2 inside blocks of the BFS order
+                                  (a data-parallel variant; not in the paper)
   access_trace, reuse_distances, quantile   Section 2.2 / Fig. 1 reuse
                                   distance of one sweep, Table 2 quantiles
 """
@@ -27,7 +29,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lms_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liblms_oracle.so")
 
-ORI, RANDOM, BFS, RDR, RBFS = 0, 1, 2, 3, 4
+ORI, RANDOM, BFS, RDR, RBFS, BRDR = 0, 1, 2, 3, 4, 5
+BRDR_BLOCK = 4096  # block size of the block RDR ordering
 DISTINCT, ACCESSES = 0, 1
 JACOBI, INPLACE = 0, 1
 
@@ -72,6 +75,7 @@ def _lib():
             "or_color_greedy": [_I32, _P_I32, _P_I32, _P_U8, _P_I32, _P_I32, _P_I32],
             "or_color_sequence": [_I32, _P_U8, _P_I32, _P_I32, _I32, _P_I32, _P_I32],
             "or_order_rbfs": [_I32, _P_I32, _P_I32, _P_I32],
+            "or_order_brdr": [_I32, _P_I32, _P_I32, _P_U8, _P_F64, _I32, _P_I32],
             "or_access_trace": [_I32, _P_I32, _P_I32, _P_U8, _I32, _P_I32, _I32, _P_I32, _P_I64],
             "or_reuse_distances": [_I64, _P_I32, _I32, _I32, _P_I64, _P_I64],
             "or_quantile": [_I64, _P_I64, ctypes.c_double, _P_I64],
@@ -194,6 +198,15 @@ def order_rbfs(row_ptr, col_idx):
     return p
 
 
+def order_brdr(row_ptr, col_idx, is_boundary, q_v, block=BRDR_BLOCK):
+    row_ptr, col_idx, bnd, q_v = _i32(row_ptr), _i32(col_idx), _u8(is_boundary), _f64(q_v)
+    n = len(row_ptr) - 1
+    p = np.empty(n, np.int32)
+    _check(_lib().or_order_brdr(n, _p(row_ptr, _P_I32), _p(col_idx, _P_I32), _p(bnd, _P_U8), _p(q_v, _P_F64),
+                                int(block), _p(p, _P_I32)), "order_brdr")
+    return p
+
+
 def order(mesh, ordering, seed=0, q_v=None):
     """Permutation new_to_old of a mesh dict for ORI/RANDOM/BFS/RDR/RBFS (RDR keys from its coordinates)."""
     n = mesh["n"]
@@ -209,6 +222,10 @@ def order(mesh, ordering, seed=0, q_v=None):
         return order_rdr(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], q_v)
     if ordering == RBFS:
         return order_rbfs(mesh["row_ptr"], mesh["col_idx"])
+    if ordering == BRDR:
+        if q_v is None:
+            q_v = vertex_quality(n, mesh["tri"], mesh["xy"])
+        return order_brdr(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], q_v)
     raise ValueError(ordering)
 
 

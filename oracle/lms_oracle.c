@@ -33,6 +33,9 @@
  *       colour" is the in-place sweep that a coloured Gauss-Seidel reproduces.
  *   or_order_rbfs - the reversed breadth-first order (BFS visit order read
  *       backwards) that Section 2 reports from Munson and Hovland's study.
+ *   or_order_brdr - a blocked variant of Algorithm 2 that is not in the paper:
+ *       the BFS order cut into blocks of consecutive positions, Algorithm 2
+ *       applied to each block's own subgraph, blocks kept in BFS order.
  *   or_access_trace / or_reuse_distances / or_quantile - Section 2.2's reuse
  *       distance over the data accesses of one sweep (Fig. 3: a vertex, then
  *       its neighbours), and the quantiles of Table 2 (the X quantile is the
@@ -538,5 +541,78 @@ int or_quantile(int64_t m, const int64_t* values, double X, int64_t* out) {
     if (k > m) k = m;
     *out = s[k - 1];
     free(s);
+    return OR_OK;
+}
+
+static int cmp_int32_asc(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Block RDR.  bfs = the BFS order (or_order_bfs); block j = the vertices at
+ * BFS positions [j*block, (j+1)*block).  For each block in turn: its interior
+ * vertices by increasing (quality, id) are the walk seeds; a walk from vertex i
+ * orders i if needed, marks it processed, and repeatedly lists i's unprocessed
+ * neighbours that lie in the same block by increasing (quality, id), orders the
+ * ones not yet ordered, and continues from the first of them; block members no
+ * walk ordered follow in ascending id.  With block >= n this is Algorithm 2;
+ * with block = 1 it is the BFS order.
+ */
+int or_order_brdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                  const double* q_v, int32_t block, int32_t* new_to_old) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !q_v || !new_to_old || block <= 0) return OR_ERR_ARG;
+    int32_t max_deg = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > max_deg) max_deg = row_ptr[v + 1] - row_ptr[v];
+    int32_t* bfs = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* blk = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* seeds = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* l = (int32_t*)malloc(sizeof(int32_t) * (size_t)(max_deg + 1));
+    uint8_t* processed = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* sorted = (uint8_t*)calloc((size_t)n, 1);
+    if (!bfs || !blk || !seeds || !l || !processed || !sorted) {
+        free(bfs); free(blk); free(seeds); free(l); free(processed); free(sorted);
+        return OR_ERR_OOM;
+    }
+    int rc = or_order_bfs(n, row_ptr, col_idx, bfs);
+    if (rc != OR_OK) {
+        free(bfs); free(blk); free(seeds); free(l); free(processed); free(sorted);
+        return rc;
+    }
+    for (int32_t k = 0; k < n; ++k) blk[bfs[k]] = k / block;
+    g_key_q = q_v;
+    int32_t next_num = 0;
+    for (int32_t start = 0; start < n; start += block) {
+        const int32_t end = start + block < n ? start + block : n, j = start / block;
+        int32_t ns = 0;
+        for (int32_t k = start; k < end; ++k)
+            if (!is_boundary[bfs[k]]) seeds[ns++] = bfs[k];
+        qsort(seeds, (size_t)ns, sizeof(int32_t), cmp_key);
+        for (int32_t si = 0; si < ns; ++si) {
+            int32_t i = seeds[si];
+            if (processed[i]) continue;
+            if (!sorted[i]) { new_to_old[next_num++] = i; sorted[i] = 1; }
+            processed[i] = 1;
+            for (;;) {
+                int32_t m = 0;   /* unprocessed neighbours of i in block j, by increasing key */
+                for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                    if (!processed[col_idx[e]] && blk[col_idx[e]] == j) l[m++] = col_idx[e];
+                if (m == 0) break;
+                qsort(l, (size_t)m, sizeof(int32_t), cmp_key);
+                for (int32_t t = 0; t < m; ++t)
+                    if (!sorted[l[t]]) { new_to_old[next_num++] = l[t]; sorted[l[t]] = 1; }
+                i = l[0];
+                processed[i] = 1;
+            }
+        }
+        /* members no walk reached, ascending id */
+        int32_t nl = 0;
+        for (int32_t k = start; k < end; ++k)
+            if (!sorted[bfs[k]]) seeds[nl++] = bfs[k];
+        qsort(seeds, (size_t)nl, sizeof(int32_t), cmp_int32_asc);
+        for (int32_t t = 0; t < nl; ++t) { new_to_old[next_num++] = seeds[t]; sorted[seeds[t]] = 1; }
+    }
+    free(bfs); free(blk); free(seeds); free(l); free(processed); free(sorted);
     return OR_OK;
 }
