@@ -64,6 +64,12 @@ extern "C" {
                         unordered neighbours by increasing (quality, id) */
 #define LMS_RBFS 4   /* reversed BFS: the LMS_BFS visit order read backwards (the ordering Section 2
                         reports from Munson and Hovland's study) */
+#define LMS_BRDR 5   /* block RDR, a data-parallel variant of Algorithm 2 that is not in the paper: the
+                        LMS_BFS order cut into blocks of LMS_BRDR_BLOCK consecutive positions, Algorithm 2
+                        applied to each block's own subgraph (walks never leave the block; members no
+                        walk reached follow in ascending id), blocks kept in BFS order.  Every reuse
+                        stays within about two blocks, as for BFS, while most are as short as RDR's */
+#define LMS_BRDR_BLOCK 4096
 
 /* reuse-distance measures (lms_reuse_profile) */
 #define LMS_REUSE_DISTINCT 0 /* distinct elements accessed between two accesses to one element (Section 2.2) */
@@ -125,7 +131,7 @@ int lms_validate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
 
 /*
  * Vertex ordering on the host (Section 4.2, Algorithm 2; Section 5.2.1).
- * q_v: [n] per-vertex quality (Section 3.2), required for LMS_RDR and ignored
+ * q_v: [n] per-vertex quality (Section 3.2), required for LMS_RDR and LMS_BRDR and ignored
  * otherwise.  new_to_old: [n] output, new_to_old[k] = original id stored at
  * position k; always a permutation (Theorem 1; vertices no RDR walk reaches
  * are appended in ascending id).  [host]

@@ -23,10 +23,11 @@ from . import _build
 
 FP64, FP32 = 0, 1
 KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
-ORI, RANDOM, BFS, RDR, RBFS = 0, 1, 2, 3, 4
+ORI, RANDOM, BFS, RDR, RBFS, BRDR = 0, 1, 2, 3, 4, 5
+BRDR_BLOCK = 4096  # LMS_BRDR_BLOCK
 JACOBI, COLORED_GS, INPLACE_STATIC = 0, 1, 2
 REUSE_DISTINCT, REUSE_ACCESSES = 0, 1
-ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS}
+ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS, "brdr": BRDR}
 MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS, "inplace_static": INPLACE_STATIC}
 PRECISIONS = {"fp64": FP64, "fp32": FP32}
 
@@ -204,7 +205,7 @@ def validate(row_ptr, col_idx, is_boundary, tri=None):
 
 
 def order_host(row_ptr, col_idx, is_boundary, ordering, seed=0, q_v=None):
-    """lms_order_host: new_to_old of ORI / RANDOM / BFS / RDR / RBFS (RDR needs q_v)."""
+    """lms_order_host: new_to_old of ORI / RANDOM / BFS / RDR / RBFS / BRDR (RDR and BRDR need q_v)."""
     rp, ci, b = _arr(row_ptr, np.int32), _arr(col_idx, np.int32), _arr(is_boundary, np.uint8)
     q = _arr(q_v, np.float64) if q_v is not None else None
     n = len(rp) - 1

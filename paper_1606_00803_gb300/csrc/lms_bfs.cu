@@ -24,6 +24,8 @@
 // independent clusters.  Frontier data written by one CTA and read by another
 // go through L2 (st.global + ld.global.cg after a release/acquire cluster
 // barrier), never through a possibly stale L1 line.
+#include <math_constants.h>
+
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -253,7 +255,156 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(BfsArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ block RDR
+
+constexpr int kBrdrThreads = 512;
+constexpr int kBrdrMaxDeg = 64;  // rows of the walk are sorted in a per-thread array of this size
+
+__device__ __forceinline__ bool key_greater(double qa, int32_t ia, double qb, int32_t ib) {
+    return qa > qb || (qa == qb && ia > ib);
+}
+
+// Ascending sort of `count` (key, id) pairs in shared memory (bitonic network over `cap`, a power of
+// two >= count; slots past count hold (+inf, INT_MAX) and stay last).
+__device__ void sort_keys(double* kq, int32_t* kid, int32_t count, int32_t cap) {
+    for (int32_t i = count + threadIdx.x; i < cap; i += blockDim.x) {
+        kq[i] = CUDART_INF;
+        kid[i] = INT_MAX;
+    }
+    __syncthreads();
+    for (int32_t k = 2; k <= cap; k <<= 1)
+        for (int32_t j = k >> 1; j > 0; j >>= 1) {
+            for (int32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+                const int32_t p = i ^ j;
+                if (p <= i) continue;
+                const bool up = (i & k) == 0;
+                if (key_greater(kq[i], kid[i], kq[p], kid[p]) == up) {
+                    const double tq = kq[i];
+                    kq[i] = kq[p];
+                    kq[p] = tq;
+                    const int32_t ti = kid[i];
+                    kid[i] = kid[p];
+                    kid[p] = ti;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// One CTA per block of BFS positions [start, end) of graph g (vertices from v0): Algorithm 2 on the
+// block's own subgraph.  The block's interior vertices are sorted by (quality, id) in shared memory; one
+// thread walks (flags in shared memory, indexed by BFS position within the block); the members no walk
+// reached are sorted by id and appended.
+__global__ void __launch_bounds__(kBrdrThreads) k_block_rdr(BrdrArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* kq = reinterpret_cast<double*>(smem);
+    int32_t* kid = reinterpret_cast<int32_t*>(kq + a.cap);
+    uint8_t* done = reinterpret_cast<uint8_t*>(kid + a.cap);
+    uint8_t* placed = done + a.cap;
+    __shared__ int32_t s_count, s_placed;
+    for (int32_t b = blockIdx.x; b < a.n_blocks; b += gridDim.x) {
+        const int4 blk = a.blocks[b];  // (v0, start, end, unused)
+        const int32_t v0 = blk.x, start = blk.y, len = blk.z - blk.y;
+        const int32_t* members = a.bfs + v0 + start;
+        int32_t* out = a.out + v0 + start;
+        if (threadIdx.x == 0) s_count = 0;
+        for (int32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            done[i] = 0;
+            placed[i] = 0;
+        }
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const int32_t v = members[i];
+            if (!a.is_boundary[v]) {
+                const int32_t k = atomicAdd(&s_count, 1);
+                kq[k] = a.q[v];
+                kid[k] = v;
+            }
+        }
+        __syncthreads();
+        sort_keys(kq, kid, s_count, a.cap);
+        if (threadIdx.x == 0) {
+            int32_t cnt = 0;
+            int32_t l[kBrdrMaxDeg];
+            double lq[kBrdrMaxDeg];
+            auto local = [&](int32_t u) { return a.bfs_pos[u] - start; };  // position within the block
+            auto place = [&](int32_t u, int32_t lu) {
+                if (!placed[lu]) {
+                    placed[lu] = 1;
+                    out[cnt++] = u;
+                }
+            };
+            // l <- unprocessed neighbours of w inside the block, by increasing (quality, id)
+            auto gather = [&](int32_t w) {
+                int32_t m = 0;
+                for (int32_t e = a.row_ptr[w]; e < a.row_ptr[w + 1]; ++e) {
+                    const int32_t u = a.col_idx[e];
+                    const int32_t lu = local(u);
+                    if (lu < 0 || lu >= len || done[lu]) continue;
+                    const double qu = a.q[u];
+                    int32_t k = m++;
+                    while (k > 0 && key_greater(lq[k - 1], l[k - 1], qu, u)) {
+                        l[k] = l[k - 1];
+                        lq[k] = lq[k - 1];
+                        --k;
+                    }
+                    l[k] = u;
+                    lq[k] = qu;
+                }
+                return m;
+            };
+            const int32_t seeds = s_count;
+            for (int32_t si = 0; si < seeds; ++si) {
+                const int32_t sd = kid[si];
+                const int32_t ls = local(sd);
+                if (done[ls]) continue;
+                place(sd, ls);
+                done[ls] = 1;
+                int32_t m = gather(sd);
+                while (m > 0) {
+                    for (int32_t k = 0; k < m; ++k) place(l[k], local(l[k]));
+                    const int32_t w = l[0];
+                    done[local(w)] = 1;
+                    m = gather(w);
+                }
+            }
+            s_placed = cnt;
+            s_count = 0;
+        }
+        __syncthreads();
+        // members no walk reached, ascending id
+        for (int32_t i = threadIdx.x; i < len; i += blockDim.x)
+            if (!placed[i]) {
+                const int32_t k = atomicAdd(&s_count, 1);
+                kq[k] = 0.0;
+                kid[k] = members[i];
+            }
+        __syncthreads();
+        const int32_t rest = s_count;
+        sort_keys(kq, kid, rest, a.cap);
+        for (int32_t k = threadIdx.x; k < rest; k += blockDim.x) out[s_placed + k] = kid[k];
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+size_t block_rdr_smem(int32_t cap) { return size_t(cap) * (8 + 4 + 2); }
+
+cudaError_t launch_block_rdr(const BrdrArgs& a, int sms, cudaStream_t stream) {
+    if (a.n_blocks <= 0) return cudaSuccess;
+    const size_t smem = block_rdr_smem(a.cap);
+    cudaError_t e = cudaFuncSetAttribute(k_block_rdr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_block_rdr, kBrdrThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(a.n_blocks, std::max(1, per_sm) * sms));
+    k_block_rdr<<<grid, kBrdrThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int block_rdr_max_degree() { return kBrdrMaxDeg; }
 
 int bfs_cluster_size(int32_t max_graph_vertices) {
     // one CTA per small graph; a large graph gets a cluster of 8 CTAs

@@ -287,45 +287,76 @@ struct lms_mesh_s {
 namespace {
 
 // Breadth-first orderings on the device (k_bfs) of k graphs with vertex offsets voff (host; NULL:
-// one graph of n vertices) over the device CSR rp/ci with global ids; out (host, [n]) receives the
-// global new_to_old.  Scratch comes from the allocator and is released before returning.
-int device_bfs(const Allocator& al, cudaStream_t s, const int32_t* rp, const int32_t* ci, int32_t n,
-               int32_t k, const int64_t* voff, int32_t* out) {
+// one graph of n vertices) over the device CSR rp/ci with global ids.  With q != NULL (device vertex
+// qualities) and is_boundary (device flags), each BFS order is then cut into blocks of LMS_BRDR_BLOCK
+// positions and reordered by block RDR (k_block_rdr).  out (host, [n]) receives the global new_to_old.
+// Scratch comes from the allocator and is released before returning.
+int device_order(const Allocator& al, cudaStream_t s, int sms, const int32_t* rp, const int32_t* ci, int32_t n,
+                 int32_t k, const int64_t* voff, const double* q, const uint8_t* is_boundary, int32_t* out) {
     Arena tmp;
     tmp.al = al;
     tmp.stream = s;
     lms::BfsArgs a{};
     int32_t* d_voff = nullptr;
+    int32_t* d_brdr = nullptr;
+    int4* d_blocks = nullptr;
+    const int32_t graphs = voff ? k : 1;
+    std::vector<int32_t> v32(graphs + 1);
+    for (int32_t g = 0; g <= graphs; ++g) v32[g] = voff ? int32_t(voff[g]) : (g == 0 ? 0 : n);
+    int32_t largest = 0;
+    for (int32_t g = 0; g < graphs; ++g) largest = std::max(largest, v32[g + 1] - v32[g]);
+    std::vector<int4> blocks;
+    if (q)
+        for (int32_t g = 0; g < graphs; ++g)
+            for (int32_t st = 0; st < v32[g + 1] - v32[g]; st += LMS_BRDR_BLOCK)
+                blocks.push_back(make_int4(v32[g], st, std::min(v32[g + 1] - v32[g], st + LMS_BRDR_BLOCK), 0));
     int rc;
     if ((rc = tmp.get(&a.out, n)) || (rc = tmp.get(&a.pos, n)) || (rc = tmp.get(&a.parent, n)) ||
-        (voff && (rc = tmp.get(&d_voff, k + 1)))) {
+        (voff && (rc = tmp.get(&d_voff, k + 1))) || (q && (rc = tmp.get(&d_brdr, n))) ||
+        (q && (rc = tmp.get(&d_blocks, blocks.size())))) {
         tmp.release_all();
         return rc;
-    }
-    int32_t largest = n;
-    std::vector<int32_t> v32;
-    if (voff) {
-        v32.resize(k + 1);
-        largest = 0;
-        for (int32_t g = 0; g <= k; ++g) v32[g] = int32_t(voff[g]);
-        for (int32_t g = 0; g < k; ++g) largest = std::max(largest, v32[g + 1] - v32[g]);
     }
     a.row_ptr = rp;
     a.col_idx = ci;
     a.voff = d_voff;
-    a.k = voff ? k : 1;
+    a.k = graphs;
     a.n_total = n;
     cudaError_t e = voff ? cudaMemcpyAsync(d_voff, v32.data(), 4 * size_t(k + 1), cudaMemcpyHostToDevice, s)
                          : cudaSuccess;
     if (!e) e = lms::launch_bfs(a, lms::bfs_cluster_size(largest), s);
-    if (!e) e = cudaMemcpyAsync(out, a.out, 4 * size_t(n), cudaMemcpyDeviceToHost, s);
+    const int32_t* result = a.out;
+    if (!e && q) {
+        lms::BrdrArgs b{};
+        b.row_ptr = rp;
+        b.col_idx = ci;
+        b.is_boundary = is_boundary;
+        b.q = q;
+        b.bfs = a.out;
+        b.bfs_pos = a.pos;
+        b.blocks = d_blocks;
+        b.n_blocks = int32_t(blocks.size());
+        b.cap = 1;
+        while (b.cap < std::min(largest, int32_t(LMS_BRDR_BLOCK))) b.cap <<= 1;
+        b.out = d_brdr;
+        e = cudaMemcpyAsync(d_blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, s);
+        if (!e) e = lms::launch_block_rdr(b, sms, s);
+        result = d_brdr;
+    }
+    if (!e) e = cudaMemcpyAsync(out, result, 4 * size_t(n), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     tmp.release_all();
     if (e) {
-        lms::set_error_detail(std::string("device BFS: ") + cudaGetErrorString(e));
+        lms::set_error_detail(std::string(q ? "device block RDR: " : "device BFS: ") + cudaGetErrorString(e));
         return LMS_ERR_CUDA;
     }
     return LMS_OK;
+}
+
+int max_row(const int32_t* rp, int64_t n) {
+    int32_t m = 0;
+    for (int64_t v = 0; v < n; ++v) m = std::max(m, rp[v + 1] - rp[v]);
+    return m;
 }
 
 // Move the mesh to storage order `perm_new` (new_to_old): CSR rows gathered from the original
@@ -755,13 +786,13 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
 }
 
 int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
-    if (!h || ordering < LMS_ORI || ordering > LMS_RBFS) return LMS_ERR_ARG;
-    if (ordering == LMS_RDR && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
+    if (!h || ordering < LMS_ORI || ordering > LMS_BRDR) return LMS_ERR_ARG;
+    if ((ordering == LMS_RDR || ordering == LMS_BRDR) && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
     LMS_CUDA(cudaStreamSynchronize(h->stream));  // earlier work does not count towards the ordering time
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<double> q;
-    if (ordering == LMS_RDR) {
+    if (ordering == LMS_RDR || ordering == LMS_BRDR) {
         // keys: Section 3.2 vertex qualities of the current positions, FP64, original labels
         LMS_TRY(positions_fp64_original(h));
         LMS_TRY(check_launch(lms::launch_tri_quality_exact(h->ntri, h->d_tri0, h->d_xy64, h->d_qt, h->stream),
@@ -776,8 +807,13 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     std::vector<int32_t> p(h->n);
     if (ordering == LMS_BFS || ordering == LMS_RBFS) {
         // level-synchronous search on the device, equal to the sequential one
-        LMS_TRY(device_bfs(h->arena.al, h->stream, h->d_rp0, h->d_ci0, h->n, 1, nullptr, p.data()));
+        LMS_TRY(device_order(h->arena.al, h->stream, h->sms, h->d_rp0, h->d_ci0, h->n, 1, nullptr, nullptr, nullptr,
+                             p.data()));
         if (ordering == LMS_RBFS) std::reverse(p.begin(), p.end());
+    } else if (ordering == LMS_BRDR && max_row(h->rp.data(), h->n) <= lms::block_rdr_max_degree()) {
+        // device BFS, then Algorithm 2 inside each block on the device, keys already in d_qv
+        LMS_TRY(device_order(h->arena.al, h->stream, h->sms, h->d_rp0, h->d_ci0, h->n, 1, nullptr, h->d_qv, h->d_bnd0,
+                             p.data()));
     } else {
         LMS_TRY(lms::order_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), q.empty() ? nullptr : q.data(),
                                     ordering, seed, p.data()));
@@ -1344,7 +1380,7 @@ extern "C" {
 
 int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint64_t seed, void* cuda_stream,
                      lms_batch* out) {
-    if (!out || !meshes || k <= 0 || ordering < LMS_ORI || ordering > LMS_RBFS) return LMS_ERR_ARG;
+    if (!out || !meshes || k <= 0 || ordering < LMS_ORI || ordering > LMS_BRDR) return LMS_ERR_ARG;
     *out = nullptr;
     // validate in parallel
     std::vector<int> status(k, LMS_OK);
@@ -1358,7 +1394,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
                     const lms_mesh_desc& d = meshes[m];
                     int rc = lms::validate_mesh(d.n, d.row_ptr, d.col_idx, d.is_boundary, d.ntri, d.tri);
                     if (rc == LMS_OK && (!d.xy || !all_finite(d.xy, 2 * int64_t(d.n)))) rc = LMS_ERR_ARG;
-                    if (rc == LMS_OK && ordering == LMS_RDR && (d.ntri <= 0 || !d.tri)) rc = LMS_ERR_NO_TRIANGLES;
+                    if (rc == LMS_OK && (ordering == LMS_RDR || ordering == LMS_BRDR) && (d.ntri <= 0 || !d.tri)) rc = LMS_ERR_NO_TRIANGLES;
                     status[m] = rc;
                 }
             });
@@ -1385,7 +1421,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     for (int32_t m = 0; m < k; ++m) {
         b->voff[m + 1] = b->voff[m] + meshes[m].n;
         eoff[m + 1] = eoff[m] + meshes[m].row_ptr[meshes[m].n];
-        toff[m + 1] = toff[m] + (ordering == LMS_RDR ? meshes[m].ntri : 0);
+        toff[m + 1] = toff[m] + ((ordering == LMS_RDR || ordering == LMS_BRDR) ? meshes[m].ntri : 0);
         for (int32_t v = 0; v < meshes[m].n; ++v) b->n_int += meshes[m].is_boundary[v] ? 0 : 1;
     }
     b->n_total = b->voff[k];
@@ -1412,7 +1448,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
             bnd0[vo + v] = d.is_boundary[v] ? 1 : 0;
         }
         for (int32_t e = 0; e < d.row_ptr[d.n]; ++e) ci0[eo + e] = vo + d.col_idx[e];
-        if (ordering == LMS_RDR)
+        if (ordering == LMS_RDR || ordering == LMS_BRDR)
             for (int64_t i = 0; i < 3 * int64_t(d.ntri); ++i) tri0[3 * toff[m] + i] = vo + d.tri[i];
         std::memcpy(xy0.data() + 2 * size_t(vo), d.xy, 16 * size_t(d.n));
         double cx, cy, s;
@@ -1459,9 +1495,21 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         cudaMemcpyAsync(b->d_cs, b->cs.data(), 32 * size_t(k), cudaMemcpyHostToDevice, s))
         return fail_orig(LMS_ERR_CUDA);
 
-    // RDR keys: Section 3.2 vertex qualities in FP64 on the device
+    // RDR keys: Section 3.2 vertex qualities in FP64 on the device (block RDR keeps them there when its
+    // walks run on the device)
     std::vector<double> q;
-    if (ordering == LMS_RDR) {
+    Arena keys;
+    keys.al = b->arena.al;
+    keys.stream = s;
+    double* d_qv_keep = nullptr;
+    bool brdr_device = false;
+    if (ordering == LMS_BRDR) {
+        int32_t max_deg = 0;
+        for (int32_t m = 0; m < k; ++m) max_deg = std::max(max_deg, max_row(meshes[m].row_ptr, meshes[m].n));
+        brdr_device = max_deg <= lms::block_rdr_max_degree();
+        if (brdr_device && (rc = keys.get(&d_qv_keep, N))) return fail_orig(rc);
+    }
+    if (ordering == LMS_RDR || ordering == LMS_BRDR) {
         std::vector<int32_t> vt_ptr, vt_idx;
         build_incidence(N, T, tri0.data(), vt_ptr, vt_idx);
         int32_t *d_tri = nullptr, *d_vp = nullptr, *d_vi = nullptr;
@@ -1472,6 +1520,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         if ((rc = tmp.get(&d_tri, 3 * size_t(T))) || (rc = tmp.get(&d_vp, N + 1)) ||
             (rc = tmp.get(&d_vi, 3 * size_t(T))) || (rc = tmp.get(&d_qt, T)) || (rc = tmp.get(&d_qv, N))) {
             tmp.release_all();
+            keys.release_all();
             return fail_orig(rc);
         }
         q.resize(N);
@@ -1480,10 +1529,12 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         if (!e) e = cudaMemcpyAsync(d_vi, vt_idx.data(), 12 * size_t(T), cudaMemcpyHostToDevice, s);
         if (!e) e = lms::launch_tri_quality_exact(T, d_tri, b->d_xy64, d_qt, s);
         if (!e) e = lms::launch_vertex_quality_exact(N, d_vp, d_vi, d_qt, d_qv, s);
+        if (!e && d_qv_keep) e = cudaMemcpyAsync(d_qv_keep, d_qv, 8 * size_t(N), cudaMemcpyDeviceToDevice, s);
         if (!e) e = cudaMemcpyAsync(q.data(), d_qv, 8 * size_t(N), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         tmp.release_all();
         if (e) {
+            keys.release_all();
             lms::set_error_detail(std::string("batch quality: ") + cudaGetErrorString(e));
             return fail_orig(LMS_ERR_CUDA);
         }
@@ -1491,9 +1542,12 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     // per-mesh orderings: breadth-first ones on the device (one search per mesh), the others on
     // host threads
     b->perm.resize(N);
-    if (ordering == LMS_BFS || ordering == LMS_RBFS) {
-        if ((rc = device_bfs(b->arena.al, s, d_rp0, d_ci0, N, k, b->voff.data(), b->perm.data())))
-            return fail_orig(rc);
+    if (ordering == LMS_BFS || ordering == LMS_RBFS || (ordering == LMS_BRDR && brdr_device)) {
+        rc = device_order(b->arena.al, s, b->sms, d_rp0, d_ci0, N, k, b->voff.data(),
+                          ordering == LMS_BRDR ? d_qv_keep : nullptr, ordering == LMS_BRDR ? d_bnd0 : nullptr,
+                          b->perm.data());
+        keys.release_all();
+        if (rc) return fail_orig(rc);
         if (ordering == LMS_RBFS)
             for (int32_t m = 0; m < k; ++m) std::reverse(b->perm.begin() + b->voff[m], b->perm.begin() + b->voff[m + 1]);
     } else {

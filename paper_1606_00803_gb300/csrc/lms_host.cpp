@@ -14,7 +14,9 @@
 //          unvisited id;
 //   RANDOM - Fisher-Yates, i = n-1 .. 1, j = splitmix64() mod (i+1);
 //   RBFS - the BFS visit order read backwards (the reversed breadth-first order
-//          Section 2 reports from Munson and Hovland).
+//          Section 2 reports from Munson and Hovland);
+//   BRDR - block RDR, a data-parallel variant of Algorithm 2 (not in the paper):
+//          Algorithm 2 inside blocks of LMS_BRDR_BLOCK consecutive BFS positions.
 //
 // The reuse-distance profile follows Section 2.2 and Table 2: the access trace of one sweep
 // (each interior vertex in storage order, optionally itself, then its stored row - the pattern of
@@ -22,9 +24,11 @@
 // accesses, in between), and Table 2's quantiles (the k-th smallest, k = ceil(X m) in double,
 // clamped to [1, m]).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <deque>
 #include <vector>
 
@@ -169,6 +173,69 @@ void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     }
     for (int32_t v = 0; v < n; ++v) place(v);  // vertices no walk reached, ascending id
 }
+// Block RDR (a data-parallel variant of Algorithm 2; not in the paper): the BFS order `bfs` cut into
+// blocks of `block` consecutive positions, Algorithm 2 run on each block's own subgraph (walks only
+// through vertices of the block; members no walk reached follow in ascending id), blocks kept in BFS
+// order.  Blocks are independent, so host threads take them in turn.
+void order_brdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                const double* q, int32_t block, const int32_t* bfs, int32_t* out) {
+    KeyLess less{q};
+    std::vector<int32_t> blk(n);
+    for (int32_t k = 0; k < n; ++k) blk[bfs[k]] = k / block;
+    std::vector<uint8_t> done(n, 0), placed(n, 0);
+    const int32_t nblocks = (n + block - 1) / block;
+    std::atomic<int32_t> next(0);
+    auto worker = [&]() {
+        std::vector<int32_t> seeds, l, rest;
+        for (int32_t j; (j = next++) < nblocks;) {
+            const int32_t start = j * block, end = std::min(n, start + block);
+            seeds.clear();
+            for (int32_t k = start; k < end; ++k)
+                if (!is_boundary[bfs[k]]) seeds.push_back(bfs[k]);
+            std::sort(seeds.begin(), seeds.end(), less);
+            int32_t pos = start;
+            auto place = [&](int32_t v) {
+                if (!placed[v]) {
+                    placed[v] = 1;
+                    out[pos++] = v;
+                }
+            };
+            auto gather = [&](int32_t v) {  // unprocessed neighbours inside the block, by increasing key
+                l.clear();
+                for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                    const int32_t u = col_idx[e];
+                    if (blk[u] != j || done[u]) continue;
+                    l.push_back(u);
+                    for (size_t k = l.size() - 1; k > 0 && less(l[k], l[k - 1]); --k) std::swap(l[k], l[k - 1]);
+                }
+            };
+            for (int32_t sd : seeds) {
+                if (done[sd]) continue;
+                place(sd);
+                done[sd] = 1;
+                gather(sd);
+                while (!l.empty()) {
+                    for (int32_t u : l) place(u);
+                    const int32_t w = l.front();
+                    done[w] = 1;
+                    gather(w);
+                }
+            }
+            rest.clear();
+            for (int32_t k = start; k < end; ++k)
+                if (!placed[bfs[k]]) rest.push_back(bfs[k]);
+            std::sort(rest.begin(), rest.end());
+            for (int32_t v : rest) place(v);
+        }
+    };
+    // a thread per 16 blocks at most: small meshes (a batch's) stay on the calling thread
+    const unsigned nt = std::max(1u, std::min({16u, std::thread::hardware_concurrency(), unsigned(nblocks / 16)}));
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+}
+
 // Reuse distances of one sweep's access trace.  Distinct-element distances use a Fenwick tree over
 // access times holding a 1 at the latest access of every element seen so far: for an access at
 // time t to an element last accessed at time p, the elements accessed in between are the marks
@@ -333,6 +400,13 @@ int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
             order_bfs(n, row_ptr, col_idx, new_to_old);
             std::reverse(new_to_old, new_to_old + n);
             return LMS_OK;
+        case LMS_BRDR: {
+            if (!q_v || !is_boundary || (!col_idx && row_ptr[n] > 0)) return LMS_ERR_ARG;
+            std::vector<int32_t> bfs(n);
+            order_bfs(n, row_ptr, col_idx, bfs.data());
+            order_brdr(n, row_ptr, col_idx, is_boundary, q_v, LMS_BRDR_BLOCK, bfs.data(), new_to_old);
+            return LMS_OK;
+        }
         default:
             return LMS_ERR_ARG;
     }

@@ -102,6 +102,25 @@ struct BfsArgs {
 int bfs_cluster_size(int32_t max_graph_vertices);
 cudaError_t launch_bfs(const BfsArgs& a, int cluster, cudaStream_t stream);
 
+// Block RDR on the device (k_block_rdr): blocks[b] = (graph's first vertex v0, first and end BFS
+// position of the block within the graph, unused); bfs / bfs_pos = a BfsArgs out / pos pair; out receives
+// the new_to_old (global ids) at the same places as bfs.  cap = a power of two >= the largest block.
+struct BrdrArgs {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const uint8_t* is_boundary;
+    const double* q;
+    const int32_t* bfs;
+    const int32_t* bfs_pos;
+    const int4* blocks;
+    int32_t n_blocks;
+    int32_t cap;
+    int32_t* out;
+};
+size_t block_rdr_smem(int32_t cap);
+cudaError_t launch_block_rdr(const BrdrArgs& a, int sms, cudaStream_t stream);
+int block_rdr_max_degree();  // rows longer than this need the host implementation
+
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
 // The paper's static-schedule in-place sweep over [0, a.v_end) split into `threads` contiguous blocks

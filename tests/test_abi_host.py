@@ -85,8 +85,8 @@ def test_validate_rejects_bad_meshes():
     assert lms.validate(rp, ci, b, t2) == -1
 
 
-@pytest.mark.parametrize("side", [6, 20, 57])
-@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS])
+@pytest.mark.parametrize("side", [6, 20, 57, 130])
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS, lms.BRDR])
 def test_host_ordering_matches_oracle(side, ordering):
     m = meshgen.workload(1, side=side)
     q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
@@ -128,7 +128,7 @@ def test_host_orderings_on_a_disconnected_mesh():
     xy = np.concatenate([a["xy"], b["xy"] + 3.0])
     m = dict(n=n, row_ptr=rp, col_idx=ci, is_boundary=bnd, tri=tri, xy=xy)
     q = oracle.vertex_quality(n, tri, xy)
-    for ordering in (lms.BFS, lms.RDR, lms.RANDOM):
+    for ordering in (lms.BFS, lms.RDR, lms.RANDOM, lms.BRDR):
         assert np.array_equal(lms.order_host(rp, ci, bnd, ordering, seed=9, q_v=q), oracle.order(m, ordering, 9, q))
 
 
@@ -187,3 +187,11 @@ def test_reuse_profile_rejects_bad_arguments():
     with pytest.raises(lms.LmsError) as e:
         lms.reuse_profile(m["row_ptr"], ci, m["is_boundary"])
     assert e.value.status == -2
+
+
+def test_host_block_rdr_on_many_blocks_matches_oracle():
+    # 1024 x 1024 mesh: 282 blocks, spread over host threads
+    m = meshgen.workload(1)
+    q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
+    got = lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.BRDR, q_v=q)
+    assert np.array_equal(got, oracle.order_brdr(m["row_ptr"], m["col_idx"], m["is_boundary"], q, block=lms.BRDR_BLOCK))

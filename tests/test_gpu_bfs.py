@@ -73,3 +73,37 @@ def test_reorder_times_are_reported():
             g.reorder(o)
             order_ms, layout_ms = g.last_reorder_ms()
             assert 0.0 <= order_ms < 60e3 and 0.0 <= layout_ms < 60e3
+
+
+def brdr_want(m, rp=None, ci=None):
+    rp = m["row_ptr"] if rp is None else rp
+    ci = m["col_idx"] if ci is None else ci
+    q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
+    return oracle.order_brdr(rp, ci, m["is_boundary"], q, block=lms.BRDR_BLOCK)
+
+
+@pytest.mark.parametrize("side", [5, 60, 100, 400])
+def test_device_block_rdr_single_mesh(side):
+    m = meshgen.workload(1, side=side)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(lms.BRDR)
+        assert np.array_equal(g.permutation(), brdr_want(m))
+
+
+def test_device_block_rdr_shuffled_rows_and_components():
+    a, b = meshgen.workload(1, side=90), meshgen.workload(0, side=40)
+    rp, ci = disjoint_union(a, b)
+    ci = shuffled_rows(rp, ci, 3)
+    m = dict(n=a["n"] + b["n"], row_ptr=rp, col_idx=ci, is_boundary=np.concatenate([a["is_boundary"], b["is_boundary"]]),
+             tri=np.concatenate([a["tri"], b["tri"] + a["n"]]), xy=np.concatenate([a["xy"], b["xy"] + 2.0]))
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.BRDR)
+        assert np.array_equal(g.permutation(), brdr_want(m))
+
+
+def test_device_block_rdr_batch():
+    meshes = [meshgen.generate(s, jitter=0.3, flip_frac=0.1, split_frac=0.05, seed=900 + s)
+              for s in (3, 7, 30, 64, 120, 200)]
+    with lms.Batch(meshes, ordering=lms.BRDR) as b:
+        for i, m in enumerate(meshes):
+            assert np.array_equal(b.permutation(i), brdr_want(m))

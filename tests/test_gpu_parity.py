@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 2e-6
-ORDERINGS = [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS]
+ORDERINGS = [lms.ORI, lms.RANDOM, lms.BFS, lms.RDR, lms.RBFS, lms.BRDR]
 
 
 def diag(m):
