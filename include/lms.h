@@ -178,11 +178,15 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
                void* cuda_stream, lms_handle* out);
 
 /*
- * Store the mesh under an ordering (Section 4.2 / 5.2.1): computes the
- * permutation on the host (RDR keys are the per-vertex qualities of the
- * current coordinates, computed on the device in FP64) and relabels the
- * device CSR, coordinates and triangles.  Rows keep their entry order, so
- * Jacobi results do not depend on the ordering.  seed is used by LMS_RANDOM.
+ * Store the mesh under an ordering (Section 4.2 / 5.2.1) and relabel the
+ * device CSR, coordinates and triangles.  Where the permutation is computed:
+ * LMS_BFS and LMS_RBFS on the device (level-synchronous search, equal to the
+ * sequential one); LMS_BRDR on the device (rows of at most 64 entries; longer
+ * rows use the host implementation, with the same result); LMS_RDR keys on the
+ * device (Section 3.2 qualities of the current coordinates, FP64) and its walk
+ * on the host; LMS_RANDOM and LMS_ORI on the host.  Rows keep their entry
+ * order, so Jacobi results do not depend on the ordering.  seed is used by
+ * LMS_RANDOM.  Synchronous; lms_last_reorder_ms reports the time taken.
  */
 int lms_reorder(lms_handle h, int ordering, uint64_t seed);
 
