@@ -391,7 +391,38 @@ def large_table(hbm_peak):
                     updates_per_s=n_int / (ms * 1e-3), sweep_ms=round(ms, 4), algorithmic_gbs=round(gbs, 1),
                     hbm_frac=round(gbs / hbm_peak, 3))
             g.close()
+    rows["gs_to_tol"] = gs_to_tol(m)
     return dict(workload="4096x4096 jittered grid + flips/splits (%d vertices), 20-sweep graphs" % n, rows=rows)
+
+
+def gs_to_tol(m):
+    """Coloured GS on the 4096 x 4096 mesh until the mean quality gains less than 1e-6 in a sweep (cap
+    2000), RANDOM and RDR, FP64 and FP32; the FP32 error is taken against FP64 after the same number of
+    sweeps (the FP64 sweeps equal the oracle's bit for bit)."""
+    import math
+    import numpy as np
+    import meshgen
+    import paper_1606_00803_gb300 as lms
+    diag = math.hypot(np.ptp(m["xy"][:, 0]), np.ptp(m["xy"][:, 1]))
+    out = {}
+    for oname, o in (("random", lms.RANDOM), ("rdr", lms.RDR)):
+        row = {}
+        with lms.Mesh.from_dict(m, lms.FP32) as g32:
+            g32.reorder(o, seed=meshgen.BASE_SEED + 7)
+            k32 = g32.smooth(2000, mode=lms.COLORED_GS, tol=1e-6)
+            st = g32.last_stats()
+            x32 = g32.coords()
+            row["fp32"] = dict(sweeps=k32, ms=round(st["ms"], 1), q_first=st["q_first"], q_last=st["q_last"])
+        with lms.Mesh.from_dict(m, lms.FP64) as g64:
+            g64.reorder(o, seed=meshgen.BASE_SEED + 7)
+            k64 = g64.smooth(2000, mode=lms.COLORED_GS, tol=1e-6)
+            st = g64.last_stats()
+            row["fp64"] = dict(sweeps=k64, ms=round(st["ms"], 1), q_first=st["q_first"], q_last=st["q_last"])
+            g64.set_coords(m["xy"])
+            g64.smooth(k32, mode=lms.COLORED_GS)
+            row["fp32_err_vs_fp64_same_sweeps_over_diag"] = float(np.abs(x32 - g64.coords()).max() / diag)
+        out[oname] = row
+    return out
 
 
 def log(msg):

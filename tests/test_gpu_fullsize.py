@@ -139,3 +139,27 @@ def test_workload3_batch_device_bfs_sampled():
         for i in sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 0, 511, 77, 300}):
             m = meshes[i]
             assert np.array_equal(b.permutation(i), oracle.order_bfs(m["row_ptr"], m["col_idx"]))
+
+
+def test_workload4_device_block_rdr():
+    # 4096 x 4096 mesh: 4,505 blocks ordered on the device, one CTA each
+    m = meshgen.workload(4)
+    q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
+    want = oracle.order_brdr(m["row_ptr"], m["col_idx"], m["is_boundary"], q, block=lms.BRDR_BLOCK)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(lms.BRDR)
+        assert np.array_equal(g.permutation(), want)
+
+
+@pytest.mark.parametrize("mode", [lms.JACOBI, lms.COLORED_GS])
+def test_workload4_fp32_within_tolerance_after_100_sweeps(mode):
+    # the FP64 device sweeps equal the oracle bit for bit (tested above and at smaller sizes), so they
+    # stand in for it at this size
+    m = meshgen.workload(4)
+    got = {}
+    for precision in (lms.FP32, lms.FP64):
+        with lms.Mesh.from_dict(m, precision) as g:
+            g.reorder(lms.RDR)
+            g.smooth(100, mode=mode)
+            got[precision] = g.coords()
+    assert np.abs(got[lms.FP32] - got[lms.FP64]).max() <= TOL32 * diag(m)
