@@ -1,10 +1,12 @@
 // lms_capi.cpp - the C ABI of liblms (declared in include/lms.h): handles,
 // device memory, storage layouts, CUDA-graph capture of sweep loops, the
-// Section 5.1 stopping rule, the batched work-queue path and its autotuner.
+// Section 5.1 stopping rule, device orderings (BFS, block RDR), the batched
+// work-queue path, its autotuner and the pipelined end-to-end batch call.
 //
 // Storage layouts.  A handle keeps the mesh in one storage order at a time:
 //   - the ordering's layout (lms_reorder): position k holds original vertex
-//     new_to_old[k]; Jacobi sweeps run here;
+//     new_to_old[k]; Jacobi and the in-place static sweep run here (the
+//     latter moves the mesh back here after a coloured Gauss-Seidel);
 //   - the coloured layout (first LMS_COLORED_GS sweep after a reorder): the
 //     interior vertices sorted by (colour, position in the ordering), then the
 //     boundary vertices; each colour is one contiguous range, so one colour

@@ -1,6 +1,7 @@
-// lms_host.cpp - host-side logic of liblms: mesh validation, the four vertex
-// orderings and the first-fit colouring.  Pure C++, no device work; built with
-// -ffp-contract=off (the only floating-point work here is comparing keys).
+// lms_host.cpp - host-side logic of liblms: mesh validation, the vertex
+// orderings, the first-fit colouring and the reuse-distance profile.  Pure C++,
+// no device work; built with -ffp-contract=off (the only floating-point work
+// here is comparing keys).
 //
 // Orderings follow Aupy, Park & Raghavan, "Locality-Aware Laplacian Mesh
 // Smoothing": ORI and BFS as compared in Section 5.2.1, a random ordering as in
