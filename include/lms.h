@@ -271,6 +271,14 @@ void lms_destroy(lms_handle h);
 int lms_jacobi_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                        double* xy, double* xy_tmp, int32_t iters, void* cuda_stream);
 
+/*
+ * Bounds checks of debug builds.  A library built with -DLMS_CHECKS tests every neighbour id against
+ * the vertex count before a sweep or ordering kernel uses it, counts each failure on the device and
+ * skips that access.  *enabled = 1 in such a build (0 otherwise, where the count is always 0);
+ * *violations = failures since the last reset; reset != 0 clears the count.  Any pointer may be NULL.
+ */
+int lms_debug_checks(int32_t* enabled, uint64_t* violations, int32_t reset);
+
 /* Text of the last CUDA error seen by this thread (empty if none). [host] */
 const char* lms_last_error_detail(void);
 
@@ -280,6 +288,15 @@ const char* lms_last_error_detail(void);
  * q[i] must equal the IEEE quotient.  Host arrays of `count` entries.
  */
 int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q);
+
+/*
+ * Self-test of the bounded device-side waits (the tile-copy waits of the staged kernel): one device
+ * thread waits on an mbarrier phase that nothing completes, gives up after about wait_us microseconds
+ * (1 .. 2,000,000; counted in cycles of the top SM clock, so longer at lower clocks) and records the
+ * expiry, which the host reports as LMS_ERR_TIMEOUT - the status a real expired wait returns.  The CUDA
+ * context stays usable.  Returns LMS_ERR_TIMEOUT on success of the self-test, LMS_ERR_ARG, LMS_ERR_CUDA.
+ */
+int lms_selftest_timeout(int32_t wait_us);
 
 /*
  * Batched FP32 smoothing of many independent meshes in one persistent

@@ -84,6 +84,8 @@ _SIGS = {
     "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
+    "lms_selftest_timeout": ([_I32], ctypes.c_int),
+    "lms_debug_checks": ([_PI32, ctypes.POINTER(ctypes.c_uint64), _I32], ctypes.c_int),
     "lms_batch_create": ([_I32, ctypes.POINTER(MeshDesc), ctypes.c_int, _U64, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "lms_batch_smooth": ([_P, _I32], ctypes.c_int),
     "lms_batch_get_coords": ([_P, _I32, _P], ctypes.c_int),
@@ -103,7 +105,7 @@ _handle = None
 
 
 def library_path():
-    return _build.LIB
+    return _build.LIB_CHECKED if os.environ.get("LMS_LIBRARY") == "checked" else _build.LIB
 
 
 def _lib():
@@ -112,7 +114,8 @@ def _lib():
     if _handle is None:
         # launch configurations picked by lms_batch_autotune persist next to the library
         os.environ.setdefault("LMS_AUTOTUNE_CACHE", os.path.join(_build.OUT_DIR, "autotune_cache.txt"))
-        path = _build.build()
+        # LMS_LIBRARY=checked loads the debug build with device bounds checks (built on demand)
+        path = _build.build(checked=os.environ.get("LMS_LIBRARY") == "checked")
         lib = ctypes.CDLL(path)
         for name, (args, res) in _SIGS.items():
             fn = getattr(lib, name)
@@ -243,6 +246,18 @@ def reuse_profile(row_ptr, col_idx, is_boundary, new_to_old=None, with_vertex=Tr
                                     ctypes.byref(acc), ctypes.byref(reu), _ptr(hist)), "lms_reuse_profile")
     return {"quantiles": {float(x): int(v) for x, v in zip(qs, out_q)}, "mean": mean.value, "accesses": acc.value,
             "reuses": reu.value, "hist": hist}
+
+
+def debug_checks(reset=False):
+    """lms_debug_checks: (bounds checks compiled in, failed checks since the last reset)."""
+    en, v = ctypes.c_int32(), ctypes.c_uint64()
+    _check(_lib().lms_debug_checks(ctypes.byref(en), ctypes.byref(v), int(bool(reset))), "lms_debug_checks")
+    return bool(en.value), v.value
+
+
+def selftest_timeout(wait_us=2000):
+    """lms_selftest_timeout: status of a bounded device wait that is made to expire (LMS_ERR_TIMEOUT = -7)."""
+    return _lib().lms_selftest_timeout(int(wait_us))
 
 
 def selftest_div64(s, d):

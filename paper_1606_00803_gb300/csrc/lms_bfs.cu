@@ -30,6 +30,7 @@
 #include <climits>
 #include <cstdint>
 
+#include "lms_device.cuh"
 #include "lms_internal.h"
 
 namespace lms {
@@ -132,10 +133,11 @@ __device__ __forceinline__ void load_fast_row(const BfsArgs& a, int32_t e0, int3
 #pragma unroll
     for (int k = 0; k < kBfsFastDeg; ++k) {
         r.u[k] = k < deg ? __ldg(a.col_idx + e0 + k) : -1;
+        if (r.u[k] >= 0 && !LMS_CHECK(r.u[k] < a.n_total)) r.u[k] = -1;
     }
 #pragma unroll
     for (int k = 0; k < kBfsFastDeg; ++k)
-        if (k < deg && __ldcg(a.parent + r.u[k]) == i) r.child |= 1u << k;
+        if (r.u[k] >= 0 && __ldcg(a.parent + r.u[k]) == i) r.child |= 1u << k;
 }
 
 __global__ void __launch_bounds__(kBfsThreads) k_bfs(BfsArgs a) {
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(BfsArgs a) {
                 const int32_t e1 = __ldg(a.row_ptr + w + 1);
                 for (int32_t e = __ldg(a.row_ptr + w); e < e1; ++e) {
                     const int32_t u = __ldg(a.col_idx + e);
+                    if (!LMS_CHECK(u >= 0 && u < a.n_total)) continue;
                     if (__ldcg(a.pos + u) < 0) atomicMin(a.parent + u, i);
                 }
             }
@@ -200,7 +203,10 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(BfsArgs a) {
                     load_fast_row(a, e0, deg, i, r);
                     cnt += __popc(r.child);
                 } else {
-                    for (int32_t e = e0; e < e0 + deg; ++e) cnt += __ldcg(a.parent + __ldg(a.col_idx + e)) == i;
+                    for (int32_t e = e0; e < e0 + deg; ++e) {
+                        const int32_t u = __ldg(a.col_idx + e);
+                        if (LMS_CHECK(u >= 0 && u < a.n_total)) cnt += __ldcg(a.parent + u) == i;
+                    }
                 }
             }
             int32_t cta_total = 0;
@@ -235,11 +241,11 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(BfsArgs a) {
                     int32_t c = 0;
                     for (int32_t e = e0; e < e0 + deg; ++e) {
                         const int32_t u = __ldg(a.col_idx + e);
-                        if (__ldcg(a.parent + u) != i) continue;
+                        if (!LMS_CHECK(u >= 0 && u < a.n_total) || __ldcg(a.parent + u) != i) continue;
                         int32_t below = 0;
                         for (int32_t f = e0; f < e0 + deg; ++f) {
                             const int32_t x = __ldg(a.col_idx + f);
-                            below += x < u && __ldcg(a.parent + x) == i;
+                            below += x >= 0 && x < a.n_total && x < u && __ldcg(a.parent + x) == i;
                         }
                         a.out[v0 + o + below] = u;
                         a.pos[u] = o + below;
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(kBrdrThreads) k_block_rdr(BrdrArgs a) {
                 int32_t m = 0;
                 for (int32_t e = a.row_ptr[w]; e < a.row_ptr[w + 1]; ++e) {
                     const int32_t u = a.col_idx[e];
+                    if (!LMS_CHECK(u >= 0 && u < a.n_total)) continue;
                     const int32_t lu = local(u);
                     if (lu < 0 || lu >= len || done[lu]) continue;
                     const double qu = a.q[u];
@@ -388,6 +395,8 @@ __global__ void __launch_bounds__(kBrdrThreads) k_block_rdr(BrdrArgs a) {
 }
 
 }  // namespace
+
+LMS_CHECK_ACCESSOR(check_violations_orderings)
 
 size_t block_rdr_smem(int32_t cap) { return size_t(cap) * (8 + 4 + 2); }
 

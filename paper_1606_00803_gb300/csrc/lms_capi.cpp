@@ -338,6 +338,7 @@ int device_order(const Allocator& al, cudaStream_t s, int sms, const int32_t* rp
         b.bfs_pos = a.pos;
         b.blocks = d_blocks;
         b.n_blocks = int32_t(blocks.size());
+        b.n_total = n;
         b.cap = 1;
         while (b.cap < std::min(largest, int32_t(LMS_BRDR_BLOCK))) b.cap <<= 1;
         b.out = d_brdr;
@@ -530,6 +531,7 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
     a.dst = h->d_xy[dst];
     a.v_begin = 0;
     a.v_end = h->n;
+    a.n_vertices = h->n;
     a.recip = h->d_recip;
     return a;
 }
@@ -1096,6 +1098,40 @@ int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double*
     return LMS_OK;
 }
 
+int lms_selftest_timeout(int32_t wait_us) {
+    if (wait_us < 1 || wait_us > 2000000) return LMS_ERR_ARG;
+    int dev = 0, khz = 0;
+    LMS_CUDA(cudaGetDevice(&dev));
+    LMS_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long bound = static_cast<long long>(wait_us) * std::max(khz, 1) / 1000;  // cycles at the top clock
+    Arena A;
+    int32_t* d_err = nullptr;
+    LMS_TRY(A.get(&d_err, 1));
+    int32_t err = 0;
+    cudaError_t e = cudaMemset(d_err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = lms::launch_wait_selftest(bound, d_err, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    A.release_all();
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("wait selftest: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    if (err) {
+        lms::set_error_detail("bounded device wait expired (self-test)");
+        return LMS_ERR_TIMEOUT;
+    }
+    return LMS_OK;
+}
+
+int lms_debug_checks(int32_t* enabled, uint64_t* violations, int32_t reset) {
+    if (enabled) *enabled = lms::checks_enabled() ? 1 : 0;
+    const unsigned long long v = lms::check_violations_kernels(reset != 0) +
+                                 lms::check_violations_orderings(reset != 0) +
+                                 lms::check_violations_noalloc(reset != 0);
+    if (violations) *violations = v;
+    return LMS_OK;
+}
+
 const char* lms_last_error_detail(void) { return lms::error_detail().c_str(); }
 
 void lms_destroy(lms_handle h) { delete h; }
@@ -1292,6 +1328,7 @@ SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
     a.n_items = b->n_items;
     a.queue = b->d_queue + slot;
     a.v_end = int32_t(b->n_total);
+    a.n_vertices = int32_t(b->n_total);
     return a;
 }
 

@@ -5,8 +5,34 @@
 
 #include "lms_internal.h"
 
+// Bounds checks of debug builds (nvcc -DLMS_CHECKS): LMS_CHECK(cond) counts a failed check in this
+// translation unit's g_check_violations and yields false, so the caller skips the access; in release
+// builds it is the constant true and compiles away.  Each kernel source defines a host accessor with
+// LMS_CHECK_ACCESSOR(name).
 namespace lms {
 namespace dev {
+#ifdef LMS_CHECKS
+static __device__ unsigned long long g_check_violations;
+__device__ __forceinline__ bool check_ok(bool c) {
+    if (!c) atomicAdd(&g_check_violations, 1ull);
+    return c;
+}
+#define LMS_CHECK(cond) (::lms::dev::check_ok(cond))
+#define LMS_CHECK_ACCESSOR(name)                                                                  \
+    unsigned long long name(bool reset) {                                                         \
+        unsigned long long v = 0;                                                                 \
+        cudaMemcpyFromSymbol(&v, ::lms::dev::g_check_violations, sizeof(v));                      \
+        if (reset) {                                                                              \
+            const unsigned long long zero = 0;                                                    \
+            cudaMemcpyToSymbol(::lms::dev::g_check_violations, &zero, sizeof(zero));              \
+        }                                                                                         \
+        return v;                                                                                 \
+    }
+#else
+#define LMS_CHECK(cond) true
+#define LMS_CHECK_ACCESSOR(name) \
+    unsigned long long name(bool) { return 0; }
+#endif
 
 __device__ __forceinline__ bool boundary_bit(const uint32_t* __restrict__ bits, int32_t v) {
     return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;

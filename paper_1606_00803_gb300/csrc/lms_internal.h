@@ -54,6 +54,7 @@ struct SweepArgs {
     const void* src;               // double2 / float2 positions read
     void* dst;                     // positions written (== src for the in-place coloured sweep)
     int32_t v_begin, v_end;        // vertex range of a static launch
+    int32_t n_vertices;            // vertices addressable by col_idx (bounds checks of debug builds)
     const int2* items;             // work-queue tiles (batched)
     int32_t n_items;
     int32_t* queue;                // work-queue counter for this sweep
@@ -82,6 +83,8 @@ struct StagedArgs {
     int32_t* err;                  // set to 1 when a bounded wait expired
 };
 size_t staged_smem_bytes(int precision, int32_t tile_cap, int32_t e_cap);
+// One thread waits (bounded by bound_cycles) on an mbarrier phase that never completes; sets *err = 1.
+cudaError_t launch_wait_selftest(long long bound_cycles, int32_t* err, cudaStream_t stream);
 cudaError_t launch_sweep_staged(int precision, bool in_place, const StagedArgs& a, int grid, int block,
                                 cudaStream_t stream);
 int staged_occupancy(int precision, bool in_place, int block, int32_t tile_cap, int32_t e_cap);
@@ -115,11 +118,18 @@ struct BrdrArgs {
     const int4* blocks;
     int32_t n_blocks;
     int32_t cap;
+    int32_t n_total;               // vertices addressable by col_idx (bounds checks of debug builds)
     int32_t* out;
 };
 size_t block_rdr_smem(int32_t cap);
 cudaError_t launch_block_rdr(const BrdrArgs& a, int sms, cudaStream_t stream);
 int block_rdr_max_degree();  // rows longer than this need the host implementation
+
+// Failed bounds checks counted by each kernel source in debug builds (-DLMS_CHECKS; 0 otherwise).
+unsigned long long check_violations_kernels(bool reset);
+unsigned long long check_violations_orderings(bool reset);
+unsigned long long check_violations_noalloc(bool reset);
+bool checks_enabled();
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
 cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);

@@ -54,7 +54,10 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
         int32_t u[kChunk];
         V p[kChunk];
 #pragma unroll
-        for (int g = 0; g < kChunk; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+        for (int g = 0; g < kChunk; ++g) {
+            u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+            if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+        }
 #pragma unroll
         for (int g = 0; g < kChunk; ++g)
             if (u[g] >= 0) p[g] = IN_PLACE ? src[u[g]] : __ldg(src + u[g]);
@@ -137,7 +140,9 @@ __global__ void __launch_bounds__(256) k_inplace_static(SweepArgs a, int32_t per
         if constexpr (FP64) {
             double sx = 0.0, sy = 0.0;
             for (int32_t e = e0; e < e1; ++e) {
-                const V p = __ldcg(pos + __ldg(a.col_idx + e));
+                const int32_t u = __ldg(a.col_idx + e);
+                if (!LMS_CHECK(u >= 0 && u < a.n_vertices)) continue;
+                const V p = __ldcg(pos + u);
                 sx = __dadd_rn(sx, p.x);
                 sy = __dadd_rn(sy, p.y);
             }
@@ -146,7 +151,9 @@ __global__ void __launch_bounds__(256) k_inplace_static(SweepArgs a, int32_t per
         } else {
             float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
             for (int32_t e = e0; e < e1; ++e) {
-                const V p = __ldcg(pos + __ldg(a.col_idx + e));
+                const int32_t u = __ldg(a.col_idx + e);
+                if (!LMS_CHECK(u >= 0 && u < a.n_vertices)) continue;
+                const V p = __ldcg(pos + u);
                 kahan_add(sx, cx, p.x);
                 kahan_add(sy, cy, p.y);
             }
@@ -199,7 +206,10 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
                     int32_t u[CHUNK];
                     float2 p[CHUNK];
 #pragma unroll
-                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                    for (int g = 0; g < CHUNK; ++g) {
+                        u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                        if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+                    }
 #pragma unroll
                     for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
 #pragma unroll
@@ -220,7 +230,10 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
                     int32_t u[CHUNK];
                     float2 p[CHUNK];
 #pragma unroll
-                    for (int g = 0; g < CHUNK; ++g) u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                    for (int g = 0; g < CHUNK; ++g) {
+                        u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                        if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+                    }
 #pragma unroll
                     for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
 #pragma unroll
@@ -731,6 +744,16 @@ cudaError_t launch_div_selftest(int32_t count, const double* s, const int32_t* d
     if (count <= 0) return cudaSuccess;
     k_div_selftest<<<blocks_for(count, 256), 256, 0, stream>>>(count, s, d, recip, q);
     return cudaGetLastError();
+}
+
+LMS_CHECK_ACCESSOR(check_violations_kernels)
+
+bool checks_enabled() {
+#ifdef LMS_CHECKS
+    return true;
+#else
+    return false;
+#endif
 }
 
 }  // namespace lms

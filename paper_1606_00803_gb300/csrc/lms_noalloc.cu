@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "lms_device.cuh"
 #include "lms_internal.h"
 
 namespace {
@@ -47,7 +48,9 @@ __global__ void __launch_bounds__(kNoAllocTile) k_jacobi_noalloc(int32_t n, cons
                 const int32_t e0 = row_ptr[v], e1 = row_ptr[v + 1];
                 double sx = 0.0, sy = 0.0;
                 for (int32_t e = e0; e < e1; ++e) {
-                    const double2 p = src[col_idx[e]];
+                    const int32_t u = col_idx[e];
+                    if (!LMS_CHECK(u >= 0 && u < n)) continue;
+                    const double2 p = src[u];
                     sx = __dadd_rn(sx, p.x);
                     sy = __dadd_rn(sy, p.y);
                 }
@@ -94,6 +97,10 @@ int noalloc_setup(int32_t** queue, int* sms) {
 }
 
 }  // namespace
+
+namespace lms {
+LMS_CHECK_ACCESSOR(check_violations_noalloc)
+}  // namespace lms
 
 extern "C" int lms_jacobi_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                   const uint8_t* is_boundary, double* xy, double* xy_tmp, int32_t iters,

@@ -60,12 +60,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// bounded wait for the phase with the given parity; false when the bound expired
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait for the phase with the given parity; false when the bound (in clock cycles) expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long bound = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > bound) return false;
     return true;
+}
+
+// Self-test of the bounded wait: one thread waits for an mbarrier phase that nothing completes (no
+// thread arrives, no copy is issued), gives up after `bound` cycles and records where it gave up in
+// *err, as a tile-copy wait of k_sweep_staged would.
+__global__ void k_wait_selftest(long long bound, int32_t* err) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, bound)) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -282,6 +292,11 @@ int occupancy_t(int block, size_t smem) {
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(long long bound_cycles, int32_t* err, cudaStream_t stream) {
+    k_wait_selftest<<<1, 1, 0, stream>>>(bound_cycles, err);
+    return cudaGetLastError();
+}
 
 size_t staged_smem_bytes(int precision, int32_t tile_cap, int32_t e_cap) {
     const size_t rp = ((size_t(tile_cap) + 8 + 3) & ~size_t(3)) * 4;

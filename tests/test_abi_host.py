@@ -195,3 +195,13 @@ def test_host_block_rdr_on_many_blocks_matches_oracle():
     q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
     got = lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.BRDR, q_v=q)
     assert np.array_equal(got, oracle.order_brdr(m["row_ptr"], m["col_idx"], m["is_boundary"], q, block=lms.BRDR_BLOCK))
+
+
+def test_timeout_selftest_rejects_bad_bounds_without_device_work():
+    assert lms.selftest_timeout(0) == -1
+    assert lms.selftest_timeout(3_000_000) == -1
+
+
+def test_release_build_reports_no_bounds_checks():
+    enabled, violations = lms.debug_checks()
+    assert enabled is False and violations == 0
