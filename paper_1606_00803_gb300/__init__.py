@@ -86,6 +86,7 @@ _SIGS = {
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_timeout": ([_I32], ctypes.c_int),
     "lms_debug_checks": ([_PI32, ctypes.POINTER(ctypes.c_uint64), _I32], ctypes.c_int),
+    "lms_jacobi_noalloc": ([_I32, _P, _P, _P, _P, _P, _I32, _P], ctypes.c_int),
     "lms_batch_create": ([_I32, ctypes.POINTER(MeshDesc), ctypes.c_int, _U64, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "lms_batch_smooth": ([_P, _I32], ctypes.c_int),
     "lms_batch_get_coords": ([_P, _I32, _P], ctypes.c_int),
@@ -246,6 +247,23 @@ def reuse_profile(row_ptr, col_idx, is_boundary, new_to_old=None, with_vertex=Tr
                                     ctypes.byref(acc), ctypes.byref(reu), _ptr(hist)), "lms_reuse_profile")
     return {"quantiles": {float(x): int(v) for x, v in zip(qs, out_q)}, "mean": mean.value, "accesses": acc.value,
             "reuses": reu.value, "hist": hist}
+
+
+def jacobi_noalloc(row_ptr, col_idx, is_boundary, xy, xy_tmp, iters, stream=None):
+    """lms_jacobi_noalloc on caller-owned device tensors: row_ptr / col_idx int32, is_boundary uint8,
+    xy / xy_tmp float64 (2n values each, contiguous, on the current CUDA device).  Positions are updated in
+    xy; returns nothing and raises LmsError on a bad status."""
+    tensors = (row_ptr, col_idx, is_boundary, xy, xy_tmp)
+    wanted = ("torch.int32", "torch.int32", "torch.uint8", "torch.float64", "torch.float64")
+    for t, w in zip(tensors, wanted):
+        if not hasattr(t, "data_ptr") or not t.is_cuda or str(t.dtype) != w or not t.is_contiguous():
+            raise ValueError("jacobi_noalloc takes contiguous CUDA tensors (int32 CSR, uint8 flags, float64 xy)")
+    n = row_ptr.numel() - 1
+    if xy.numel() != 2 * n or xy_tmp.numel() != 2 * n or is_boundary.numel() != n:
+        raise ValueError("tensor sizes do not match the CSR")
+    s = current_stream() if stream is None else int(stream)
+    _check(_lib().lms_jacobi_noalloc(n, _ptr(row_ptr), _ptr(col_idx), _ptr(is_boundary), _ptr(xy), _ptr(xy_tmp),
+                                     int(iters), ctypes.c_void_p(s)), "lms_jacobi_noalloc")
 
 
 def debug_checks(reset=False):

@@ -205,3 +205,9 @@ def test_timeout_selftest_rejects_bad_bounds_without_device_work():
 def test_release_build_reports_no_bounds_checks():
     enabled, violations = lms.debug_checks()
     assert enabled is False and violations == 0
+
+
+def test_binding_declares_a_signature_for_every_entry_point():
+    # an entry point without argtypes would pass 64-bit pointers as 32-bit ints
+    missing = [n for n in declared_entry_points() if n not in lms._SIGS]
+    assert not missing, missing

@@ -53,9 +53,7 @@ ci = torch.tensor(m["col_idx"], dtype=torch.int32, device=dev)
 bd = torch.tensor(m["is_boundary"], dtype=torch.uint8, device=dev)
 x = torch.tensor(m["xy"], dtype=torch.float64, device=dev).reshape(-1)
 tmp = torch.empty_like(x)
-rc = lms._lib().lms_jacobi_noalloc(m["n"], rp.data_ptr(), ci.data_ptr(), bd.data_ptr(), x.data_ptr(), tmp.data_ptr(), 4,
-                                    torch.cuda.current_stream().cuda_stream)
-assert rc == 0
+lms.jacobi_noalloc(rp, ci, bd, x, tmp, 4)
 torch.cuda.synchronize()
 enabled, violations = lms.debug_checks()
 assert violations == 0, violations
