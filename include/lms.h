@@ -202,7 +202,8 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
 
 /*
  * Sweep kernel of a handle: LMS_KERNEL_DIRECT (default; one thread per vertex - FP32 Jacobi runs on the
- * persistent work-queue sweep over 512-vertex tiles, rows read 4 entries at a time; the other sweeps on a
+ * persistent work-queue sweep over 128- to 512-vertex tiles chosen by mesh size, as do the colour passes of
+ * FP32 coloured GS (128-vertex tiles), rows read 4 entries at a time; the other sweeps on a
  * one-pass grid, FP64 rows read 4 entries at a time; tile ignored) or LMS_KERNEL_STAGED (tile = vertices
  * per work item, a multiple of 32 up to 4096; the handle's initial tile is 512 for FP32 and 256 for FP64);
  * block = 128 or 256 threads (the work-queue sweep always uses 128).  Results do not depend on the choice

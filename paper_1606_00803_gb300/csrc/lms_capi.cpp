@@ -426,16 +426,23 @@ int build_items(lms_mesh_s* h) {
     }
     LMS_CUDA(cudaMemcpyAsync(h->d_items4, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
                              h->stream));
-    // FP32 Jacobi work queue: tiles of kQueueTile vertices and row offsets carrying the boundary flag
-    constexpr int32_t kQueueTile = 512;
+    // FP32 work queue: tiles and row offsets carrying the boundary flag.  Jacobi tiles: the largest of
+    // 512, 256, 128 vertices that still gives every resident CTA of the queue kernel four tiles (a mesh of
+    // ~1M vertices is latency-bound and sweeps 28% faster in 128-vertex tiles; from ~5M vertices up the
+    // larger tiles win by a few per cent).  A colour range holds a seventh of the mesh or so, so its tiles
+    // are 128 vertices (one 128-thread round each; 5-28% faster colour passes than 512).
+    const int64_t resident = int64_t(std::max(1, lms::batch_sweep_occupancy(128, 4))) * std::max(1, h->sms);
+    int32_t kQueueTile = 512;
+    while (kQueueTile > 128 && (int64_t(h->n) + kQueueTile - 1) / kQueueTile < 4 * resident) kQueueTile >>= 1;
+    constexpr int32_t kColourTile = 128;
     std::vector<int2> items2;
     for (int32_t v = 0; v < h->n; v += kQueueTile) items2.push_back(make_int2(v, std::min(h->n, v + kQueueTile)));
     const int32_t n_all2 = int32_t(items2.size());
     h->item2_col_ofs.assign(1, 0);
     if (h->coloured_layout)
         for (int32_t c = 0; c < h->ncolours; ++c) {
-            for (int32_t v = h->colour_ofs[c]; v < h->colour_ofs[c + 1]; v += kQueueTile)
-                items2.push_back(make_int2(v, std::min(h->colour_ofs[c + 1], v + kQueueTile)));
+            for (int32_t v = h->colour_ofs[c]; v < h->colour_ofs[c + 1]; v += kColourTile)
+                items2.push_back(make_int2(v, std::min(h->colour_ofs[c + 1], v + kColourTile)));
             h->item2_col_ofs.push_back(int32_t(items2.size()) - n_all2);
         }
     if (int64_t(items2.size()) > h->items2_cap) {
