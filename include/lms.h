@@ -331,7 +331,9 @@ int lms_batch_set_all_coords(lms_batch b, const double* xy);
  * (same layout, as lms_batch_get_all_coords).  The meshes are split into `groups` runs of whole meshes
  * whose vertex counts ramp up and down by a factor of 4 (1 : 4 : 16 : ... : 4 : 1); each group's input
  * copy, sweeps and output copy are ordered, and the copies of one group overlap the sweeps of the others
- * (two copy streams, one compute stream), so only the first input and the last output copy are exposed.  The
+ * (two copy streams; groups alternate between the caller's stream and a second compute stream, so one
+ * group's last sweeps overlap the next group's first), so only the first input and the last output copy
+ * are exposed.  The
  * result equals lms_batch_set_all_coords + lms_batch_smooth(iters) + lms_batch_get_all_coords bit for
  * bit, and afterwards the batch holds it as after those calls.  The copies overlap only when xy_in and
  * xy_out are page-locked.  groups in [1, k] (the SELL kernel always uses 1).  Synchronous.  Returns

@@ -1188,8 +1188,9 @@ struct lms_batch_s {
     GraphCache graphs;
     int64_t last_launches = 0;
     int sms = 0;
-    // lms_batch_run: copy streams and per-group events
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    // lms_batch_run: copy streams, a second compute stream and per-group events
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_c2 = nullptr;
+    cudaEvent_t ev_join = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_done;
     cudaEvent_t ev_start = nullptr;
 
@@ -1197,11 +1198,14 @@ struct lms_batch_s {
         if (stream) cudaStreamSynchronize(stream);
         if (s_in) cudaStreamSynchronize(s_in);
         if (s_out) cudaStreamSynchronize(s_out);
+        if (s_c2) cudaStreamSynchronize(s_c2);
         graphs.clear();
         arena.release_all();
         for (cudaEvent_t e : ev_in) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_done) cudaEventDestroy(e);
         if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s_c2) cudaStreamDestroy(s_c2);
         if (s_in) cudaStreamDestroy(s_in);
         if (s_out) cudaStreamDestroy(s_out);
         if (cap) cudaStreamDestroy(cap);
@@ -1856,7 +1860,9 @@ int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iter
     if (!b->s_in) {
         LMS_CUDA(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
         LMS_CUDA(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+        LMS_CUDA(cudaStreamCreateWithFlags(&b->s_c2, cudaStreamNonBlocking));
         LMS_CUDA(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
+        LMS_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
     }
     while (int32_t(b->ev_in.size()) < groups) {
         cudaEvent_t e0, e1;
@@ -1898,9 +1904,10 @@ int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iter
     const int grid = batch_grid(b);
     const int fin = iters & 1;
     // earlier work on the caller's stream (which may read d_fixed) comes first
+    LMS_CUDA(cudaMemsetAsync(b->d_err + 1, 0, sizeof(int32_t), s));
     LMS_CUDA(cudaEventRecord(b->ev_start, s));
     LMS_CUDA(cudaStreamWaitEvent(b->s_in, b->ev_start, 0));
-    LMS_CUDA(cudaMemsetAsync(b->d_err + 1, 0, sizeof(int32_t), s));
+    LMS_CUDA(cudaStreamWaitEvent(b->s_c2, b->ev_start, 0));
     for (int32_t g = 0; g < groups; ++g) {
         const int64_t v0 = vt[g], nv = vt[g + 1] - vt[g];
         LMS_CUDA(cudaMemcpyAsync(b->d_fixed + 2 * v0, xy_in + 2 * v0, 16 * size_t(nv), cudaMemcpyHostToDevice, b->s_in));
@@ -1937,14 +1944,19 @@ int lms_batch_run(lms_batch b, const double* xy_in, double* xy_out, int32_t iter
             b->graphs.execs[key] = exec;
             b->graphs.kernels[key] = kernels;
         }
-        LMS_CUDA(cudaStreamWaitEvent(s, b->ev_in[g], 0));
-        LMS_CUDA(cudaGraphLaunch(exec, s));
-        LMS_CUDA(cudaEventRecord(b->ev_done[g], s));
+        // groups alternate between two compute streams, so the tail of one group's sweeps overlaps the
+        // next group's (their meshes, tiles and queue counters are disjoint)
+        cudaStream_t cs = (g & 1) ? b->s_c2 : s;
+        LMS_CUDA(cudaStreamWaitEvent(cs, b->ev_in[g], 0));
+        LMS_CUDA(cudaGraphLaunch(exec, cs));
+        LMS_CUDA(cudaEventRecord(b->ev_done[g], cs));
         LMS_CUDA(cudaStreamWaitEvent(b->s_out, b->ev_done[g], 0));
         const int64_t v0 = vt[g], nv = vt[g + 1] - vt[g];
         LMS_CUDA(cudaMemcpyAsync(xy_out + 2 * v0, b->d_xy64 + 2 * v0, 16 * size_t(nv), cudaMemcpyDeviceToHost, b->s_out));
         kernels_total += kernels;
     }
+    LMS_CUDA(cudaEventRecord(b->ev_join, b->s_out));
+    LMS_CUDA(cudaStreamWaitEvent(s, b->ev_join, 0));  // later calls on the caller's stream see every group
     LMS_CUDA(cudaStreamSynchronize(b->s_out));
     b->last_launches = kernels_total;
     b->cur = fin;
