@@ -500,7 +500,7 @@ def run_ours(args, dist):
     ms_step = ms_total / args.steps
     units_all = dist.sum(n_int * SWEEPS_PER_STEP * args.steps)
     value = units_all / (ms_total * 1e-3)
-    sweep_ms = ms_local / (args.steps * launches_per_step)
+    sweep_ms = ms_local / (args.steps * SWEEPS_PER_STEP)  # one sweep of the whole batch (one launch per chain)
     achieved = ab / (sweep_ms * 1e-3) / 1e9
 
     # end to end through the public API: page-locked host coordinates in, 50 sweeps, coordinates out, one
@@ -565,7 +565,10 @@ def run_ours(args, dist):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "kernel": {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"]}.get(
                              cfg["kernel"], "k_batch_sweep<%d>" % cfg["chunk"]),
-                         "algorithmic_bytes_per_launch": ab, "launch_ms": sweep_ms,
+                         "algorithmic_bytes_per_sweep": ab, "sweep_ms": sweep_ms,
+                         "launches_per_sweep": launches_per_step // SWEEPS_PER_STEP,
+                         "unit_note": "one sweep of the whole batch = one launch per mesh chain (two chains run "
+                                      "concurrently); achieved and traffic are per sweep",
                          "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / 7900.0},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -575,7 +578,8 @@ def run_ours(args, dist):
             "clocks": clocks,
         }
         line.update(extras)
-        line["roofline"]["traffic"] = load_traffic(line["roofline"]["kernel"], cfg)
+        line["roofline"]["traffic"] = load_traffic(line["roofline"]["kernel"], cfg,
+                                                   launches_per_step // SWEEPS_PER_STEP)
         print(json.dumps(line))
     b.close()
 
@@ -609,9 +613,9 @@ def kernel_source_digest():
     return h.hexdigest()
 
 
-def load_traffic(kernel, config):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json), when it was
-    captured from these exact sources and launch configuration; None otherwise."""
+def load_traffic(kernel, config, chains):
+    """DRAM bytes per sweep of `kernel` from the committed ncu summary (profiles/traffic.json), when it was
+    captured from these exact sources, launch configuration and chain count; None otherwise."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -621,7 +625,9 @@ def load_traffic(kernel, config):
         return None
     if any(t.get("config", {}).get(k) != config.get(k) for k in ("kernel", "block", "chunk", "tile")):
         return None
-    return t.get("dram_bytes_per_launch")
+    if t.get("launches_per_sweep") != chains:
+        return None
+    return t.get("dram_bytes_per_sweep")
 
 
 # ------------------------------------------------------------------ reference arm

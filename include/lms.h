@@ -310,7 +310,9 @@ int lms_selftest_timeout(int32_t wait_us);
 int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint64_t seed, void* cuda_stream,
                      lms_batch* out);
 
-/* `iters` Jacobi sweeps of every mesh, recorded once into a CUDA graph and replayed (asynchronous). */
+/* `iters` Jacobi sweeps of every mesh, recorded once into a CUDA graph and replayed (asynchronous).  The
+   graph holds two independent chains of sweeps over two halves of the meshes, so one half's sweep tail
+   overlaps the other half's work; lms_batch_last_launches counts both chains' launches. */
 int lms_batch_smooth(lms_batch b, int32_t iters);
 
 /* Coordinates of mesh `mesh` in its original labelling ([2 n_mesh] doubles).  Returns LMS_ERR_TIMEOUT
