@@ -258,6 +258,7 @@ struct lms_mesh_s {
     std::vector<int32_t> item_col_ofs;  // colour c: tiles [n_items_all + ofs[c], n_items_all + ofs[c+1])
     int32_t e_cap = 0;
     int32_t* d_rpf = nullptr;           // row offsets of the current layout with the boundary flag in bit 31
+    int32_t* d_order = nullptr;         // FP64: thread -> vertex map of the one-thread-per-vertex sweeps
     int2* d_items2 = nullptr;           // FP32 work-queue tiles over [0, n), then over each colour's range
     int64_t items2_cap = 0;
     int32_t n_items2 = 0;               // tiles over [0, n)
@@ -456,6 +457,36 @@ int build_items(lms_mesh_s* h) {
     LMS_CUDA(cudaMemcpyAsync(h->d_rpf, h->d_rp, sizeof(int32_t) * size_t(h->n + 1), cudaMemcpyDeviceToDevice,
                              h->stream));
     LMS_TRY(check_launch(lms::launch_flag_boundary_rows(h->n, h->d_bits, h->d_rpf, h->stream), "flag_rows"));
+    // FP64 one-thread-per-vertex sweeps: inside windows of kOrderWindow storage positions (never crossing
+    // a colour range), threads take the interior vertices by decreasing degree, then the boundary ones, so
+    // the lanes of a warp run rows of one length (the FP64 pipe issues a warp's add for every lane, idle
+    // or not).  Each vertex's arithmetic is unchanged, so results are too.
+    std::vector<int32_t> order;
+    if (h->precision == LMS_FP64) {
+        constexpr int32_t kOrderWindow = 1024;
+        order.resize(h->n);
+        std::vector<int32_t> cuts{0, h->n};
+        if (h->coloured_layout) cuts.insert(cuts.end() - 1, h->colour_ofs.begin() + 1, h->colour_ofs.end());
+        std::sort(cuts.begin(), cuts.end());
+        cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+        std::vector<int32_t> count;
+        for (size_t c = 0; c + 1 < cuts.size(); ++c)
+            for (int32_t w0 = cuts[c]; w0 < cuts[c + 1]; w0 += kOrderWindow) {
+                const int32_t w1 = std::min(cuts[c + 1], w0 + kOrderWindow);
+                int32_t maxd = 0;
+                for (int32_t k = w0; k < w1; ++k) maxd = std::max(maxd, h->rp_cur[k + 1] - h->rp_cur[k]);
+                // bucket = maxd - degree for interior vertices (largest first), maxd + 1 for boundary ones
+                count.assign(maxd + 3, 0);
+                auto bucket = [&](int32_t k) {
+                    return h->bnd[h->perm[k]] ? maxd + 1 : maxd - (h->rp_cur[k + 1] - h->rp_cur[k]);
+                };
+                for (int32_t k = w0; k < w1; ++k) ++count[bucket(k) + 1];
+                for (int32_t b = 0; b + 1 < int32_t(count.size()); ++b) count[b + 1] += count[b];
+                for (int32_t k = w0; k < w1; ++k) order[w0 + count[bucket(k)]++] = k;
+            }
+        LMS_CUDA(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int32_t) * size_t(h->n), cudaMemcpyHostToDevice,
+                                 h->stream));
+    }
     LMS_CUDA(cudaStreamSynchronize(h->stream));
     h->e_cap = e_cap;
     h->graphs.clear();
@@ -618,10 +649,12 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         SweepArgs a = sweep_args(h, src, src ^ 1);
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        a.order = h->precision == LMS_FP64 ? h->d_order : nullptr;
         return check_launch(lms::launch_sweep(h->precision, false, a, h->block, s), "sweep");
     }
     for (int32_t c = 0; c < h->ncolours; ++c) {
         SweepArgs a = sweep_args(h, base, base);
+        a.order = h->precision == LMS_FP64 ? h->d_order : nullptr;
         a.bnd_bits = nullptr;  // every vertex of a colour range is interior
         a.v_begin = h->colour_ofs[c];
         a.v_end = h->colour_ofs[c + 1];
@@ -736,7 +769,8 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     if ((rc = A.get(&h->d_rp0, n + 1)) || (rc = A.get(&h->d_ci0, std::max(1, h->nnz))) ||
         (rc = A.get(&h->d_tri0, t3)) || (rc = A.get(&h->d_vt_ptr, n + 1)) || (rc = A.get(&h->d_vt_idx, t3)) ||
         (rc = A.get(&h->d_bnd0, n)) || (rc = A.get(&h->d_w, std::max(1, ntri))) || (rc = A.get(&h->d_rp, n + 1 + 8)) || (rc = A.get(&h->d_rpf, n + 1 + 8)) ||
-        (rc = A.get(&h->d_ci, h->nnz + 8)) || (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
+        (rc = A.get(&h->d_ci, h->nnz + 8)) || (rc = A.get(&h->d_order, precision == LMS_FP64 ? n : 1)) ||
+        (rc = A.get(&h->d_tri, t3)) || (rc = A.get(&h->d_perm, n)) ||
         (rc = A.get(&h->d_tmp, n)) || (rc = A.get(&h->d_bits, (n + 31) / 32 + 8)) || (rc = A.get(&h->d_err, 1)) ||
         (rc = A.get(&h->d_xy[0], vb)) || (rc = A.get(&h->d_xy[1], vb)) || (rc = A.get(&h->d_xy_swap, vb)) ||
         (rc = A.get(&h->d_xy64, 2 * size_t(n))) || (rc = A.get(&h->d_qt, std::max(1, ntri))) ||

@@ -54,6 +54,7 @@ struct SweepArgs {
     const void* src;               // double2 / float2 positions read
     void* dst;                     // positions written (== src for the in-place coloured sweep)
     int32_t v_begin, v_end;        // vertex range of a static launch
+    const int32_t* order;          // static launch: thread i handles vertex order[i] (NULL: vertex i)
     int32_t n_vertices;            // vertices addressable by col_idx (bounds checks of debug builds)
     const int2* items;             // work-queue tiles (batched)
     int32_t n_items;

@@ -103,10 +103,13 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
         __syncthreads();
     }
-    const int32_t v = a.v_begin + static_cast<int32_t>(blockIdx.x * blockDim.x + threadIdx.x);
+    // thread -> vertex: the identity, or (a.order) a permutation of [v_begin, v_end) that groups vertices of
+    // equal degree into warps, so a warp's lanes run rows of one length
+    const int32_t i = a.v_begin + static_cast<int32_t>(blockIdx.x * blockDim.x + threadIdx.x);
+    const int32_t v = i < a.v_end && a.order != nullptr ? __ldg(a.order + i) : i;
     const bool want = a.disp2 != nullptr;
     double d2 = 0.0;
-    if (v < a.v_end && (a.bnd_bits == nullptr || !boundary_bit(a.bnd_bits, v))) {
+    if (i < a.v_end && (a.bnd_bits == nullptr || !boundary_bit(a.bnd_bits, v))) {
         d2 = smooth_vertex<FP64, IN_PLACE>(a, v, s_recip, want);
     }
     if (want) record_disp(a.disp2, d2);
