@@ -349,7 +349,7 @@ int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* 
 /*
  * Launch configuration of the batched sweep: kernel = LMS_KERNEL_*, block =
  * threads per CTA (128/256/512; staged: 128 or 256), chunk = row entries read
- * per step (direct: 1, 2, 4 or 8; staged: 1; SELL: 1, 4 or 8), tile =
+ * per step (direct: 1 to 6, or 8; staged: 1; SELL: 1, 4 or 8), tile =
  * vertices per work item, a multiple of 128 (staged: at most 4096; SELL: the
  * degree-sorting window sigma), ctas_per_sm = resident CTAs of the persistent
  * grid (0 = as many as fit).  lms_batch_autotune times the candidates on the

@@ -1707,7 +1707,7 @@ int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chu
     if (tile < 128 || tile > 65536 || (tile % 128) != 0 || ctas_per_sm < 0) return LMS_ERR_ARG;
     switch (kernel) {
         case LMS_KERNEL_DIRECT:
-            if (chunk != 1 && chunk != 2 && chunk != 4 && chunk != 8) return LMS_ERR_ARG;
+            if (chunk < 1 || chunk > 8 || chunk == 7) return LMS_ERR_ARG;
             break;
         case LMS_KERNEL_STAGED:
             if (block > 256 || chunk != 1 || tile > 4096) return LMS_ERR_ARG;
@@ -1755,7 +1755,7 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
     };
     std::vector<Cand> cands;
     for (int blk : {128, 256, 512})
-        for (int ch : {1, 2, 4, 8})
+        for (int ch : {1, 2, 3, 4, 5, 6, 8})
             for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_DIRECT, blk, ch, ti});
     for (int blk : {128, 256})
         for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti});

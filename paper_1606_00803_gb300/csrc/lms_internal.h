@@ -151,7 +151,7 @@ struct SellArgs {
 cudaError_t launch_batch_sell(const SellArgs& a, int block, int chunk, int grid, cudaStream_t stream);
 int batch_sell_occupancy(int block, int chunk);
 
-// batched work-queue sweep, rows read `chunk` (1, 2, 4 or 8) entries at a time
+// batched work-queue sweep, rows read `chunk` (1 to 6, or 8) entries at a time
 cudaError_t launch_batch_sweep(const SweepArgs& a, int block, int chunk, int grid, cudaStream_t stream);
 int batch_sweep_occupancy(int block, int chunk);  // resident CTAs per SM (0 on error)
 

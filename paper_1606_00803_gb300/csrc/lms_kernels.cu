@@ -570,7 +570,10 @@ BatchKernel batch_kernel(int chunk, bool extras) {
     switch (chunk) {
         case 1: return extras ? k_batch_sweep<1, true> : k_batch_sweep<1, false>;
         case 2: return extras ? k_batch_sweep<2, true> : k_batch_sweep<2, false>;
+        case 3: return extras ? k_batch_sweep<3, true> : k_batch_sweep<3, false>;
         case 4: return extras ? k_batch_sweep<4, true> : k_batch_sweep<4, false>;
+        case 5: return extras ? k_batch_sweep<5, true> : k_batch_sweep<5, false>;
+        case 6: return extras ? k_batch_sweep<6, true> : k_batch_sweep<6, false>;
         case 8: return extras ? k_batch_sweep<8, true> : k_batch_sweep<8, false>;
         default: return nullptr;
     }

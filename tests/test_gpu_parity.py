@@ -290,7 +290,9 @@ def small_batch(count=10):
                                     (lms.KERNEL_STAGED, 256, 1, 2048), (lms.KERNEL_STAGED, 128, 1, 128),
                                     (lms.KERNEL_DIRECT, 256, 1, 256), (lms.KERNEL_DIRECT, 512, 2, 1024),
                                     (lms.KERNEL_DIRECT, 128, 4, 512), (lms.KERNEL_DIRECT, 256, 8, 4096),
-                                    (lms.KERNEL_DIRECT, 128, 4, 128), (lms.KERNEL_SELL, 128, 1, 256),
+                                    (lms.KERNEL_DIRECT, 128, 4, 128), (lms.KERNEL_DIRECT, 128, 3, 512),
+                                    (lms.KERNEL_DIRECT, 256, 5, 256), (lms.KERNEL_DIRECT, 128, 6, 512),
+                                    (lms.KERNEL_SELL, 128, 1, 256),
                                     (lms.KERNEL_SELL, 256, 4, 1024), (lms.KERNEL_SELL, 512, 8, 2048),
                                     (lms.KERNEL_SELL, 128, 4, 128)])
 def test_batched_fp32_matches_oracle(config):
@@ -324,7 +326,7 @@ def test_batched_autotune_keeps_positions():
         before = b.all_coords()
         cfg = b.autotune()
         assert cfg["kernel"] in (lms.KERNEL_DIRECT, lms.KERNEL_STAGED, lms.KERNEL_SELL)
-        assert cfg["block"] in (128, 256, 512) and cfg["chunk"] in (1, 2, 4, 8)
+        assert cfg["block"] in (128, 256, 512) and cfg["chunk"] in (1, 2, 3, 4, 5, 6, 8)
         assert np.array_equal(b.all_coords(), before)
         b.smooth(7)
         b.smooth(8)
@@ -332,6 +334,15 @@ def test_batched_autotune_keeps_positions():
     for i, m in enumerate(meshes):
         want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 15)
         assert err(got[sum(len(x["xy"]) for x in meshes[:i]):][: m["n"]], want, m) <= TOL32
+
+
+def test_batched_config_rejects_unsupported_chunks():
+    with lms.Batch(small_batch(2), ordering=lms.ORI) as b:
+        for chunk in (0, 7, 9, -1):
+            with pytest.raises(lms.LmsError):
+                b.set_config(lms.KERNEL_DIRECT, 128, chunk, 512)
+        with pytest.raises(lms.LmsError):
+            b.set_config(lms.KERNEL_SELL, 128, 3, 512)
 
 
 def test_batched_set_coords_round_trip():
