@@ -36,7 +36,9 @@ PER_ORDERING_SWEEPS = 100
 E2E_GROUPS = 4  # mesh groups of the pipelined end-to-end call (sizes 1 : 4 : 4 : 1)
 ORDERINGS = (("ori", 0), ("random", 1), ("bfs", 2), ("rdr", 3), ("rbfs", 4), ("brdr", 5))  # LMS_ORI .. LMS_BRDR
 L2_BYTES = 129 * 2 ** 20
-FP64_OPS_PEAK_NOTE = "2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s counting an FMA as 2)"
+FP64_OPS_PEAK_NOTE = ("the FP64 unit's rate, 2 instructions/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s "
+                      "counting an FMA as 2); the sweep runs part of its correctly rounded adds and its divisions "
+                      "on 32-bit integer instructions (bit-identical), so it can exceed this rate")
 
 
 def parse_args():
@@ -134,8 +136,9 @@ def algorithmic_bytes_fp64(n, n_int, nnz, k=1):
 
 
 def fp64_ops(n_int, nnz_int):
-    """FP64 instructions of one FP64 sweep: two adds per neighbour entry, three per division (x, y)."""
-    return 2 * nnz_int + 6 * n_int
+    """IEEE FP64 operations of one FP64 sweep as Eq. 1 defines them: per interior vertex of degree k and
+    per coordinate, k - 1 additions and one division - 2 nnz_int in all."""
+    return 2 * nnz_int
 
 
 def measured_peaks():
@@ -532,6 +535,8 @@ def run_ours(args, dist):
         rdr = extras["per_ordering"]["rows"]["rdr/fp64/jacobi"]
         extras["fp64_plain"] = dict(
             workload="1024x1024, RDR, Jacobi, 100 sweeps", updates_per_s=rdr["updates_per_s"],
+            arithmetic="IEEE FP64, bit-identical to the oracle; divisions and every third add of a row on 32-bit "
+                       "integer instructions, the other adds on the FP64 unit (LMS_FP64_ARITH_MIXED3)",
             roofline=dict(bound="alu", achieved=rdr["fp64_ops_per_s"] / 1e9, peak=2 * 152 * 2.07,
                           unit="G FP64 instr/s", frac=round(rdr["fp64_ops_per_s"] / 1e9 / (2 * 152 * 2.07), 3),
                           peak_note=FP64_OPS_PEAK_NOTE),
@@ -597,16 +602,22 @@ def _braced_block(text, start):
 
 def kernel_source_digest():
     """sha256 over the source of the batched sweep kernel (k_batch_sweep), its argument struct and the
-    device helpers it calls: any change to them makes recorded counters stale."""
+    device helpers it calls (the bounds-check macros, the Kahan sum, the FP32 mean, the displacement
+    maximum): any change to them makes recorded counters stale."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1606_00803_gb300", "csrc")
     kernels = open(os.path.join(csrc, "lms_kernels.cu")).read()
     internal = open(os.path.join(csrc, "lms_internal.h")).read()
+    device = open(os.path.join(csrc, "lms_device.cuh")).read()
+    checks = device.index("#ifdef LMS_CHECKS")
     parts = [
         _braced_block(kernels, kernels.index("template <int CHUNK, bool EXTRAS>\n__global__ void __launch_bounds__(512) k_batch_sweep")),
         _braced_block(internal, internal.index("struct SweepArgs {")),
-        open(os.path.join(csrc, "lms_device.cuh")).read(),
-    ]
+        device[checks:device.index("#endif", checks)],
+    ] + [_braced_block(device, device.index(sig)) for sig in (
+        "__device__ __forceinline__ float mean_f32(", "__device__ __forceinline__ void kahan_add(",
+        "__device__ __forceinline__ unsigned long long warp_max_u64(",
+        "__device__ __forceinline__ void record_disp(")]
     h = hashlib.sha256()
     for p in parts:
         h.update(p.encode() + b"\0")

@@ -95,6 +95,18 @@ extern "C" {
                                sorted by degree into slices of 32 whose neighbour ids are stored
                                column-major; one lane per slot, coalesced id loads, no row offsets */
 
+/* where the FP64 sweep's arithmetic runs (lms_set_fp64_arith); every choice gives the IEEE
+   round-to-nearest sums and quotients, so results are identical */
+#define LMS_FP64_ARITH_FPU 0      /* FP64 instructions: adds, and the table-driven division */
+#define LMS_FP64_ARITH_INT_ADDS 1 /* neighbour sums on the integer pipes, division on the FP64 unit */
+#define LMS_FP64_ARITH_INT 2      /* sums and division on the integer pipes; zero or subnormal operands,
+                                     exponent gaps above 9 in a sum, the top binade and subnormal results
+                                     go to the FP64 unit */
+#define LMS_FP64_ARITH_MIXED2 3   /* division on the integer pipes; the add of every even row position
+                                     there too, the others on the FP64 unit (both pipes busy at once) */
+#define LMS_FP64_ARITH_MIXED3 4   /* as LMS_FP64_ARITH_MIXED2 with every third row position (the default:
+                                     fastest on GB300) */
+
 typedef struct lms_mesh_s* lms_handle;
 typedef struct lms_batch_s* lms_batch;
 
@@ -211,6 +223,13 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
  */
 int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
 
+/* Where the arithmetic of FP64 Jacobi and coloured GS sweeps (Eq. 1) runs: LMS_FP64_ARITH_* (default
+   LMS_FP64_ARITH_MIXED3).  GB300 executes FP64 instructions at a little over one lane per clock per SM and
+   32-bit integer instructions at up to 64 or 128, so moving part of the correctly rounded arithmetic to
+   integer instructions keeps both busy.  Results do not depend on the choice.  LMS_ERR_ARG for another
+   value.  [host] */
+int lms_set_fp64_arith(lms_handle h, int32_t mode);
+
 /* Global mesh quality Q (Section 3.2, FP64 reduction) of the current coordinates. */
 int lms_quality(lms_handle h, double* Q);
 
@@ -289,6 +308,15 @@ const char* lms_last_error_detail(void);
  * q[i] must equal the IEEE quotient.  Host arrays of `count` entries.
  */
 int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q);
+
+/*
+ * Diagnostics of the FP64 sweep's integer-pipe arithmetic (LMS_FP64_ARITH_INT): s[i] = a[i] + b[i] and
+ * q[i] = s[i] / d[i] (1 <= d[i]) computed on the device by those routines.  Every result must equal the
+ * IEEE round-to-nearest sum or quotient.  Finite inputs; host arrays of `count` entries.  LMS_ERR_ARG
+ * (negative count, NULL, d[i] < 1), LMS_ERR_CUDA.
+ */
+int lms_selftest_add64(int32_t count, const double* a, const double* b, double* s);
+int lms_selftest_divint64(int32_t count, const double* s, const int32_t* d, double* q);
 
 /*
  * Self-test of the bounded device-side waits (the tile-copy waits of the staged kernel): one device

@@ -27,6 +27,7 @@ ORI, RANDOM, BFS, RDR, RBFS, BRDR = 0, 1, 2, 3, 4, 5
 BRDR_BLOCK = 4096  # LMS_BRDR_BLOCK
 JACOBI, COLORED_GS, INPLACE_STATIC = 0, 1, 2
 REUSE_DISTINCT, REUSE_ACCESSES = 0, 1
+FP64_ARITH_FPU, FP64_ARITH_INT_ADDS, FP64_ARITH_INT, FP64_ARITH_MIXED2, FP64_ARITH_MIXED3 = 0, 1, 2, 3, 4
 ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS, "brdr": BRDR}
 MODES = {"jacobi": JACOBI, "gs": COLORED_GS, "colored_gs": COLORED_GS, "inplace_static": INPLACE_STATIC}
 PRECISIONS = {"fp64": FP64, "fp32": FP32}
@@ -82,8 +83,11 @@ _SIGS = {
     "lms_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
     "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
+    "lms_set_fp64_arith": ([_P, _I32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
+    "lms_selftest_add64": ([_I32, _P, _P, _P], ctypes.c_int),
+    "lms_selftest_divint64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_timeout": ([_I32], ctypes.c_int),
     "lms_debug_checks": ([_PI32, ctypes.POINTER(ctypes.c_uint64), _I32], ctypes.c_int),
     "lms_jacobi_noalloc": ([_I32, _P, _P, _P, _P, _P, _I32, _P], ctypes.c_int),
@@ -278,6 +282,24 @@ def selftest_timeout(wait_us=2000):
     return _lib().lms_selftest_timeout(int(wait_us))
 
 
+def selftest_add64(a, b):
+    """Device sums a+b by the FP64 sweep's integer-pipe addition (lms_selftest_add64)."""
+    a, b = _arr(a, np.float64), _arr(b, np.float64)
+    if a.shape != b.shape:
+        raise ValueError("a and b differ in shape")
+    s = np.empty_like(a)
+    _check(_lib().lms_selftest_add64(len(a), _ptr(a), _ptr(b), _ptr(s)), "lms_selftest_add64")
+    return s
+
+
+def selftest_divint64(s, d):
+    """Device quotients s/d by the FP64 sweep's integer-pipe division (lms_selftest_divint64)."""
+    s, d = _arr(s, np.float64), _arr(d, np.int32)
+    q = np.empty_like(s)
+    _check(_lib().lms_selftest_divint64(len(s), _ptr(s), _ptr(d), _ptr(q)), "lms_selftest_divint64")
+    return q
+
+
 def selftest_div64(s, d):
     """Device quotients s/d by the FP64 sweep's division routine (lms_selftest_div64)."""
     s, d = _arr(s, np.float64), _arr(d, np.int32)
@@ -370,6 +392,10 @@ class Mesh:
     def set_inplace_split(self, threads):
         """GPU threads of INPLACE_STATIC sweeps (0 = default, 1 = sequential Algorithm 1)."""
         _check(_lib().lms_set_inplace_split(self._handle(), int(threads)), "lms_set_inplace_split")
+
+    def set_fp64_arith(self, mode):
+        """Where FP64 sums and means run: FP64_ARITH_* (every mode gives the same results)."""
+        _check(_lib().lms_set_fp64_arith(self._handle(), int(mode)), "lms_set_fp64_arith")
 
     def last_reorder_ms(self):
         """(ordering ms, relabelled-layout ms) of the last reorder."""

@@ -199,9 +199,17 @@ void build_weights(int32_t ntri, const int32_t* tri, const std::vector<int32_t>&
     }
 }
 
+// RN(1/d), then the (high, low) words of floor((2^64 - 1) / d), d = 0..kMaxRecipDeg (lms_internal.h)
 std::vector<double> recip_table() {
-    std::vector<double> r(lms::kMaxRecipDeg + 1, 0.0);
+    std::vector<double> r(lms::kRecipTableDoubles, 0.0);
     for (int d = 1; d <= lms::kMaxRecipDeg; ++d) r[d] = 1.0 / double(d);
+    std::vector<uint32_t> words(2 * (lms::kMaxRecipDeg + 1), 0u);
+    for (int d = 1; d <= lms::kMaxRecipDeg; ++d) {
+        const uint64_t m = ~0ull / uint64_t(d);
+        words[2 * d] = uint32_t(m >> 32);
+        words[2 * d + 1] = uint32_t(m);
+    }
+    std::memcpy(r.data() + lms::kMaxRecipDeg + 1, words.data(), 4 * words.size());
     return r;
 }
 
@@ -275,6 +283,7 @@ struct lms_mesh_s {
     double last_disp = NAN, last_ms = NAN, q_first = NAN, q_last = NAN;
     double reorder_ms[2] = {NAN, NAN};  // last lms_reorder: ordering, relabelled layout
     int32_t inplace_threads = 0;        // LMS_INPLACE_STATIC split (0: one thread per resident slot)
+    int32_t fp64_arith = LMS_FP64_ARITH_MIXED3;  // where FP64 sums and means run (fastest on GB300)
 
     ~lms_mesh_s() {
         if (stream) cudaStreamSynchronize(stream);
@@ -650,7 +659,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
         a.order = h->precision == LMS_FP64 ? h->d_order : nullptr;
-        return check_launch(lms::launch_sweep(h->precision, false, a, h->block, s), "sweep");
+        return check_launch(lms::launch_sweep(h->precision, false, a, h->block, h->fp64_arith, s), "sweep");
     }
     for (int32_t c = 0; c < h->ncolours; ++c) {
         SweepArgs a = sweep_args(h, base, base);
@@ -660,7 +669,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.v_end = h->colour_ofs[c + 1];
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
-        LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, h->block, s), "sweep"));
+        LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, h->block, h->fp64_arith, s), "sweep"));
     }
     return LMS_OK;
 }
@@ -775,7 +784,7 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
         (rc = A.get(&h->d_xy[0], vb)) || (rc = A.get(&h->d_xy[1], vb)) || (rc = A.get(&h->d_xy_swap, vb)) ||
         (rc = A.get(&h->d_xy64, 2 * size_t(n))) || (rc = A.get(&h->d_qt, std::max(1, ntri))) ||
         (rc = A.get(&h->d_qv, n)) || (rc = A.get(&h->d_partials, lms::kQualityBlocks)) ||
-        (rc = A.get(&h->d_recip, lms::kMaxRecipDeg + 1)) || (rc = A.get(&h->d_state, 1)))
+        (rc = A.get(&h->d_recip, lms::kRecipTableDoubles)) || (rc = A.get(&h->d_state, 1)))
         return fail(rc);
     if (precision == LMS_FP32 && (rc = A.get(&h->d_pristine, 2 * size_t(n)))) return fail(rc);
 
@@ -912,6 +921,14 @@ int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile) {
         return LMS_ERR_ARG;
     }
     h->graphs.clear();
+    return LMS_OK;
+}
+
+int lms_set_fp64_arith(lms_handle h, int32_t mode) {
+    if (!h || mode < LMS_FP64_ARITH_FPU || mode > LMS_FP64_ARITH_MIXED3) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    if (mode != h->fp64_arith) h->graphs.clear();
+    h->fp64_arith = mode;
     return LMS_OK;
 }
 
@@ -1111,7 +1128,8 @@ int lms_last_launches(lms_handle h, int64_t* launches) {
     return LMS_OK;
 }
 
-int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q) {
+namespace {
+int selftest_div(int32_t count, const double* s, const int32_t* d, double* q, bool integer) {
     if (count < 0 || (count > 0 && (!s || !d || !q))) return LMS_ERR_ARG;
     for (int32_t i = 0; i < count; ++i)
         if (d[i] < 1) return LMS_ERR_ARG;
@@ -1120,7 +1138,7 @@ int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double*
     double *ds = nullptr, *dq = nullptr, *dr = nullptr;
     int32_t* dd = nullptr;
     int rc = LMS_OK;
-    if ((rc = A.get(&ds, count)) || (rc = A.get(&dq, count)) || (rc = A.get(&dr, lms::kMaxRecipDeg + 1)) ||
+    if ((rc = A.get(&ds, count)) || (rc = A.get(&dq, count)) || (rc = A.get(&dr, lms::kRecipTableDoubles)) ||
         (rc = A.get(&dd, count))) {
         A.release_all();
         return rc;
@@ -1129,8 +1147,41 @@ int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double*
     cudaError_t e = cudaMemcpy(ds, s, 8 * size_t(count), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dd, d, 4 * size_t(count), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dr, recip.data(), 8 * recip.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = lms::launch_div_selftest(count, ds, dd, dr, dq, nullptr);
+    if (e == cudaSuccess)
+        e = integer ? lms::launch_divint_selftest(count, ds, dd, dr, dq, nullptr)
+                    : lms::launch_div_selftest(count, ds, dd, dr, dq, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(q, dq, 8 * size_t(count), cudaMemcpyDeviceToHost);
+    A.release_all();
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("selftest: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    return LMS_OK;
+}
+}  // namespace
+
+int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q) {
+    return selftest_div(count, s, d, q, false);
+}
+
+int lms_selftest_divint64(int32_t count, const double* s, const int32_t* d, double* q) {
+    return selftest_div(count, s, d, q, true);
+}
+
+int lms_selftest_add64(int32_t count, const double* a, const double* b, double* s) {
+    if (count < 0 || (count > 0 && (!a || !b || !s))) return LMS_ERR_ARG;
+    if (count == 0) return LMS_OK;
+    Arena A;
+    double *da = nullptr, *db = nullptr, *ds = nullptr;
+    int rc = LMS_OK;
+    if ((rc = A.get(&da, count)) || (rc = A.get(&db, count)) || (rc = A.get(&ds, count))) {
+        A.release_all();
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(da, a, 8 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db, b, 8 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = lms::launch_add_selftest(count, da, db, ds, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(s, ds, 8 * size_t(count), cudaMemcpyDeviceToHost);
     A.release_all();
     if (e != cudaSuccess) {
         lms::set_error_detail(std::string("selftest: ") + cudaGetErrorString(e));

@@ -41,9 +41,10 @@ __device__ __forceinline__ bool boundary_bit(const uint32_t* __restrict__ bits, 
 // s / d for a positive integer d, correctly rounded: y = RN(1/d) from the table, q = RN(s*y), then one
 // correction q + RN(s - d*q)*y with fused operations (Markstein's division refinement, IBM J. Res. Dev.
 // 34(1), 1990).  About three FP64 operations instead of a full IEEE division; lms_selftest_div64 checks it
-// against IEEE division.
+// against IEEE division.  The refinement can miss by an ulp when the quotient is subnormal, so sums below
+// 2^-959 (biased exponent under 64; an integer test on the high word) take the IEEE division.
 __device__ __forceinline__ double div_by_count(double s, int32_t d, const double* recip) {
-    if (d <= kMaxRecipDeg) {
+    if (d <= kMaxRecipDeg && ((__double2hiint(s) >> 20) & 0x7ff) >= 64) {
         const double y = recip[d];
         const double q = __dmul_rn(s, y);
         const double r = __fma_rn(-q, static_cast<double>(d), s);

@@ -34,6 +34,10 @@ const std::string& error_detail();
 // ------------------------------------------------------------- device side
 
 constexpr int kMaxRecipDeg = 64;  // reciprocal table size for the exact FP64 division
+// The device reciprocal table (SweepArgs::recip) holds kRecipTableDoubles 8-byte slots: RN(1/d) for
+// d = 0..kMaxRecipDeg, then the integer division's words floor((2^64 - 1) / d) as (high, low) uint32
+// pairs for d = 0..kMaxRecipDeg (read as a uint32 array from slot kMaxRecipDeg + 1).
+constexpr int kRecipTableDoubles = 2 * (kMaxRecipDeg + 1);
 
 // State shared by the sweep, quality and stop-check kernels of one handle.
 struct DevState {
@@ -133,7 +137,9 @@ unsigned long long check_violations_noalloc(bool reset);
 bool checks_enabled();
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).
-cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream);
+// fp64_arith: LMS_FP64_ARITH_* (where the FP64 sums and means run; ignored for FP32)
+cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, int fp64_arith,
+                         cudaStream_t stream);
 // The paper's static-schedule in-place sweep over [0, a.v_end) split into `threads` contiguous blocks
 // (k_inplace_static); positions in a.dst, updated in place.
 cudaError_t launch_inplace_static(int precision, const SweepArgs& a, int32_t threads, cudaStream_t stream);
@@ -200,6 +206,11 @@ cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int3
                                   const double* mesh_cs, const uint32_t* bnd_bits, const double* fixed_xy,
                                   cudaStream_t stream);
 
+// Diagnostic: s[i] = RN(a[i] + b[i]) by the integer-pipe addition of the FP64 sweep (add_rn_int).
+cudaError_t launch_add_selftest(int32_t count, const double* a, const double* b, double* s, cudaStream_t stream);
+// Diagnostic: q[i] = s[i] / d[i] by the integer-pipe division of LMS_FP64_ARITH_INT (div_rn_int).
+cudaError_t launch_divint_selftest(int32_t count, const double* s, const int32_t* d, const double* recip, double* q,
+                                   cudaStream_t stream);
 // Diagnostic: q[i] = s[i] / d[i] by the table-driven exact division used in the FP64 sweep.
 cudaError_t launch_div_selftest(int32_t count, const double* s, const int32_t* d, const double* recip, double* q,
                                 cudaStream_t stream);

@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "lms_device.cuh"
+#include "lms_fp64_int.cuh"
 #include "lms_internal.h"
 
 namespace lms {
@@ -36,13 +37,53 @@ using namespace dev;
 
 
 
+// FP64 sums of Eq. 1: where each add runs (LMS_FP64_ARITH_*).  The first term needs no add: 0.0 + x is x
+// with -0 made +0.  The mixed modes send the add of row position j to the integer pipes when j is a
+// multiple of 2 (or 3) and to the FP64 unit otherwise, so both run at once; j is the same for every lane
+// of a warp at each step, so the choice never diverges.
+template <int ARITH>
+__device__ __forceinline__ bool int_add_at(int32_t j) {
+    if constexpr (ARITH == LMS_FP64_ARITH_FPU) return false;
+    else if constexpr (ARITH == LMS_FP64_ARITH_MIXED2) return (j & 1) == 0;
+    else if constexpr (ARITH == LMS_FP64_ARITH_MIXED3) return j % 3 == 0;
+    else return true;
+}
+
+template <int ARITH>
+__device__ __forceinline__ void sum_fp64(double& sx, double& sy, double2 p, int32_t j) {
+    if (j == 0) {
+        sx = plus_zero(p.x);
+        sy = plus_zero(p.y);
+    } else if (int_add_at<ARITH>(j)) {
+        sx = add_rn_int(sx, p.x);
+        sy = add_rn_int(sy, p.y);
+    } else {
+        sx = __dadd_rn(sx, p.x);
+        sy = __dadd_rn(sy, p.y);
+    }
+}
+
+// The FP64 mean s / d: on the integer pipes (LMS_FP64_ARITH_INT and the mixed modes) unless d exceeds the
+// table or the sum or
+// the quotient is zero or subnormal, else the table-driven FP64 division (itself IEEE division for tiny
+// sums).
+template <int ARITH>
+__device__ __forceinline__ double mean_fp64(double s, int32_t d, const double* recip, const uint32_t* magic) {
+    if constexpr (ARITH == LMS_FP64_ARITH_INT || ARITH == LMS_FP64_ARITH_MIXED2 || ARITH == LMS_FP64_ARITH_MIXED3) {
+        double q;
+        if (d <= kMaxRecipDeg && div_rn_int(s, d, magic, &q)) return q;
+    }
+    return div_by_count(s, d, recip);
+}
+
 // Eq. 1 for one vertex.  FP64 reads the row kChunk entries at a time - all neighbour ids, then all
 // position gathers, then the sums in row order - so a thread keeps kChunk loads in flight while its FP64
 // adds (1/64 of the FP32 rate on GB300) drain; FP32, issue-bound rather than latency-bound, reads one
-// entry at a time.  FP64: sequential sums and the correctly rounded division (bit-identical to the
-// sequential evaluation); FP32: Kahan sums.  Returns the squared displacement when asked.
-template <bool FP64, bool IN_PLACE>
-__device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, const double* recip, bool want_disp) {
+// entry at a time.  FP64: sequential sums (sum_fp64) and the correctly rounded division (bit-identical to
+// the sequential evaluation); FP32: Kahan sums.  Returns the squared displacement when asked.
+template <bool FP64, bool IN_PLACE, int ARITH>
+__device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, const double* recip,
+                                                const uint32_t* magic, bool want_disp) {
     constexpr int kChunk = FP64 ? 4 : 1;
     using V = typename std::conditional<FP64, double2, float2>::type;
     const V* src = static_cast<const V*>(a.src);
@@ -65,8 +106,7 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
         for (int g = 0; g < kChunk; ++g)
             if (u[g] >= 0) {
                 if constexpr (FP64) {
-                    dx_ = __dadd_rn(dx_, p[g].x);
-                    dy_ = __dadd_rn(dy_, p[g].y);
+                    sum_fp64<ARITH>(dx_, dy_, p[g], e + g - e0);
                 } else {
                     kahan_add(sx, cx, p[g].x);
                     kahan_add(sy, cy, p[g].y);
@@ -75,8 +115,8 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
     }
     V r;
     if constexpr (FP64) {
-        r.x = div_by_count(dx_, e1 - e0, recip);
-        r.y = div_by_count(dy_, e1 - e0, recip);
+        r.x = mean_fp64<ARITH>(dx_, e1 - e0, recip, magic);
+        r.y = mean_fp64<ARITH>(dy_, e1 - e0, recip, magic);
     } else {
         r.x = mean_f32(sx, cx, e1 - e0);
         r.y = mean_f32(sy, cy, e1 - e0);
@@ -95,12 +135,22 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
 // One thread per vertex over [v_begin, v_end).  Jacobi: src != dst, boundary vertices skipped
 // (both ping-pong buffers hold them).  Coloured GS: src == dst, every vertex of the range is
 // interior and of one colour, so no two threads touch neighbouring vertices.
-template <bool FP64, bool IN_PLACE>
+template <bool FP64, bool IN_PLACE, int ARITH>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
     __shared__ double s_recip[kMaxRecipDeg + 1];
+    constexpr bool kIntDiv = ARITH == LMS_FP64_ARITH_INT || ARITH == LMS_FP64_ARITH_MIXED2 ||
+                             ARITH == LMS_FP64_ARITH_MIXED3;
+    __shared__ uint32_t s_magic[kIntDiv ? 2 * (kMaxRecipDeg + 1) : 1];
     if (FP64) {
-        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
+        const uint32_t* words = reinterpret_cast<const uint32_t*>(a.recip + kMaxRecipDeg + 1);
+        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) {
+            s_recip[i] = a.recip[i];
+            if (kIntDiv) {
+                s_magic[2 * i] = words[2 * i];
+                s_magic[2 * i + 1] = words[2 * i + 1];
+            }
+        }
         __syncthreads();
     }
     // thread -> vertex: the identity, or (a.order) a permutation of [v_begin, v_end) that groups vertices of
@@ -110,7 +160,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     const bool want = a.disp2 != nullptr;
     double d2 = 0.0;
     if (i < a.v_end && (a.bnd_bits == nullptr || !boundary_bit(a.bnd_bits, v))) {
-        d2 = smooth_vertex<FP64, IN_PLACE>(a, v, s_recip, want);
+        d2 = smooth_vertex<FP64, IN_PLACE, ARITH>(a, v, s_recip, s_magic, want);
     }
     if (want) record_disp(a.disp2, d2);
 }
@@ -542,25 +592,55 @@ __global__ void k_div_selftest(int32_t count, const double* __restrict__ s, cons
     if (i < count) q[i] = div_by_count(s[i], d[i], recip);
 }
 
+__global__ void k_add_selftest(int32_t count, const double* __restrict__ a, const double* __restrict__ b,
+                               double* __restrict__ s) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) s[i] = add_rn_int(a[i], b[i]);
+}
+
+// q[i] = s[i] / d[i] by the integer-pipe division (FP64 table division where it declines)
+__global__ void k_divint_selftest(int32_t count, const double* __restrict__ s, const int32_t* __restrict__ d,
+                                  const double* __restrict__ recip, double* __restrict__ q) {
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(recip + kMaxRecipDeg + 1);
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) q[i] = mean_fp64<LMS_FP64_ARITH_INT>(s[i], d[i], recip, words);
+}
+
 inline unsigned blocks_for(int64_t count, int block) { return static_cast<unsigned>((count + block - 1) / block); }
 
 }  // namespace
 
-cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, cudaStream_t stream) {
+cudaError_t launch_sweep(int precision, bool in_place, const SweepArgs& a, int block, int fp64_arith,
+                         cudaStream_t stream) {
     const int32_t count = a.v_end - a.v_begin;
     if (count <= 0) return cudaSuccess;
     const unsigned grid = blocks_for(count, block);
+    using K = void (*)(SweepArgs);
+    K k = nullptr;
     if (precision == LMS_FP64) {
-        if (in_place)
-            k_sweep<true, true><<<grid, block, 0, stream>>>(a);
-        else
-            k_sweep<true, false><<<grid, block, 0, stream>>>(a);
+        switch (fp64_arith) {
+            case LMS_FP64_ARITH_FPU:
+                k = in_place ? k_sweep<true, true, LMS_FP64_ARITH_FPU> : k_sweep<true, false, LMS_FP64_ARITH_FPU>;
+                break;
+            case LMS_FP64_ARITH_INT_ADDS:
+                k = in_place ? k_sweep<true, true, LMS_FP64_ARITH_INT_ADDS> : k_sweep<true, false, LMS_FP64_ARITH_INT_ADDS>;
+                break;
+            case LMS_FP64_ARITH_INT:
+                k = in_place ? k_sweep<true, true, LMS_FP64_ARITH_INT> : k_sweep<true, false, LMS_FP64_ARITH_INT>;
+                break;
+            case LMS_FP64_ARITH_MIXED2:
+                k = in_place ? k_sweep<true, true, LMS_FP64_ARITH_MIXED2> : k_sweep<true, false, LMS_FP64_ARITH_MIXED2>;
+                break;
+            case LMS_FP64_ARITH_MIXED3:
+                k = in_place ? k_sweep<true, true, LMS_FP64_ARITH_MIXED3> : k_sweep<true, false, LMS_FP64_ARITH_MIXED3>;
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
     } else {
-        if (in_place)
-            k_sweep<false, true><<<grid, block, 0, stream>>>(a);
-        else
-            k_sweep<false, false><<<grid, block, 0, stream>>>(a);
+        k = in_place ? k_sweep<false, true, LMS_FP64_ARITH_FPU> : k_sweep<false, false, LMS_FP64_ARITH_FPU>;
     }
+    k<<<grid, block, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -742,6 +822,19 @@ cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int3
     k_batch_store_xy<<<n_items, 256, 0, stream>>>(items, item_mesh, new_to_old, src,
                                                   reinterpret_cast<double2*>(dst_orig), mesh_cs, bnd_bits,
                                                   reinterpret_cast<const double2*>(fixed_xy));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_selftest(int32_t count, const double* a, const double* b, double* s, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_add_selftest<<<blocks_for(count, 256), 256, 0, stream>>>(count, a, b, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divint_selftest(int32_t count, const double* s, const int32_t* d, const double* recip, double* q,
+                                   cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_divint_selftest<<<blocks_for(count, 256), 256, 0, stream>>>(count, s, d, recip, q);
     return cudaGetLastError();
 }
 
