@@ -616,8 +616,7 @@ def kernel_source_digest():
         device[checks:device.index("#endif", checks)],
     ] + [_braced_block(device, device.index(sig)) for sig in (
         "__device__ __forceinline__ float mean_f32(", "__device__ __forceinline__ void kahan_add(",
-        "__device__ __forceinline__ unsigned long long warp_max_u64(",
-        "__device__ __forceinline__ void record_disp(")]
+        "__device__ __forceinline__ void max_to(", "__device__ __forceinline__ void record_disp(")]
     h = hashlib.sha256()
     for p in parts:
         h.update(p.encode() + b"\0")

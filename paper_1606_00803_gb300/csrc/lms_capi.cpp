@@ -242,7 +242,7 @@ struct lms_mesh_s {
     // device, original labelling
     int32_t *d_rp0 = nullptr, *d_ci0 = nullptr, *d_tri0 = nullptr, *d_vt_ptr = nullptr, *d_vt_idx = nullptr;
     uint8_t* d_bnd0 = nullptr;
-    double* d_w = nullptr;
+    double* d_w = nullptr;              // per-triangle quality weights: doubles (FP64) or floats (FP32)
     // device, current layout
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_tri = nullptr, *d_perm = nullptr, *d_tmp = nullptr;
     uint32_t* d_bits = nullptr;
@@ -790,6 +790,7 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
 
     cudaStream_t s = h->stream;
     auto recip = recip_table();
+    std::vector<float> wf(w.begin(), w.end());  // FP32 handles: weights rounded to float
     std::vector<int32_t> ident(n);
     for (int32_t i = 0; i < n; ++i) ident[i] = i;
     auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -798,7 +799,9 @@ int lms_create(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
     if (up(h->d_rp0, h->rp.data(), 4 * size_t(n + 1)) || up(h->d_ci0, h->ci.data(), 4 * size_t(h->nnz)) ||
         up(h->d_tri0, h->tri.data(), 12 * size_t(ntri)) || up(h->d_vt_ptr, vt_ptr.data(), 4 * size_t(n + 1)) ||
         up(h->d_vt_idx, vt_idx.data(), 12 * size_t(ntri)) || up(h->d_bnd0, h->bnd.data(), size_t(n)) ||
-        up(h->d_w, w.data(), 8 * size_t(ntri)) || up(h->d_recip, recip.data(), 8 * recip.size()) ||
+        up(h->d_w, precision == LMS_FP64 ? static_cast<const void*>(w.data()) : static_cast<const void*>(wf.data()),
+           (precision == LMS_FP64 ? 8 : 4) * size_t(ntri)) ||
+        up(h->d_recip, recip.data(), 8 * recip.size()) ||
         up(h->d_perm, ident.data(), 4 * size_t(n)) || up(h->d_rp, h->rp.data(), 4 * size_t(n + 1)) ||
         up(h->d_ci, h->ci.data(), 4 * size_t(h->nnz)) || up(h->d_tri, h->tri.data(), 12 * size_t(ntri)) ||
         up(h->d_xy64, xy, 16 * size_t(n)) || cudaMemsetAsync(h->d_state, 0, sizeof(DevState), s) ||

@@ -66,19 +66,25 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
+// The largest squared displacement of a warp into *disp2 (bits of a non-negative double, which order like
+// the values); warp maxima by 32-bit shuffles.  Every warp of a sweep reports to the same word, so the atomic is issued only when the
+// warp's maximum exceeds the value already there: a plain read first, which turns hundreds of thousands
+// of same-address atomics per sweep (serialised at one L2 slice) into a handful.
+__device__ __forceinline__ void max_to(unsigned long long* disp2, unsigned long long m) {
+    if (m != 0ull && m > *reinterpret_cast<volatile unsigned long long*>(disp2)) atomicMax(disp2, m);
 }
 
 __device__ __forceinline__ void record_disp(unsigned long long* disp2, double d2) {
-    // non-negative doubles order like their bit patterns
-    unsigned long long m = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(d2)));
-    if ((threadIdx.x & 31) == 0 && m != 0ull) atomicMax(disp2, m);
+    uint32_t hi = static_cast<uint32_t>(__double2hiint(d2)), lo = static_cast<uint32_t>(__double2loint(d2));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
+        if (h > hi || (h == hi && l > lo)) {
+            hi = h;
+            lo = l;
+        }
+    }
+    if ((threadIdx.x & 31) == 0) max_to(disp2, (static_cast<unsigned long long>(hi) << 32) | lo);
 }
 
 

@@ -167,8 +167,9 @@ cudaError_t launch_vertex_quality_exact(int32_t n, const int32_t* vt_ptr, const 
                                         const double* q_t, double* q_v, cudaStream_t stream);
 // Per-sweep quality: partial sums of w_t * q_t over a fixed grid of nblocks, then a fixed-order finish.
 constexpr int kQualityBlocks = 1024;
+// w: per-triangle weights, double for FP64 positions and float for FP32 positions.
 cudaError_t launch_quality_partials(int precision, int32_t ntri, const int32_t* tri, const void* xy,
-                                    const double* w, double* partials, const DevState* state,
+                                    const void* w, double* partials, const DevState* state,
                                     cudaStream_t stream);
 // Q = (sum of partials) / n.  mode 0: store into q_cur; mode 1: Q_0 (q_first = q_prev = q_cur = Q).
 cudaError_t launch_quality_finish(const double* partials, double n, DevState* state, int mode, cudaStream_t stream);

@@ -89,6 +89,10 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
     const V* src = static_cast<const V*>(a.src);
     V* dst = static_cast<V*>(a.dst);
     const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+    // the old position for the displacement, loaded first so that its latency overlaps the gathers (in an
+    // in-place colour pass its line is being written by the pass; loaded last it stalled the warp)
+    V o{};
+    if (want_disp) o = src[v];
     double dx_ = 0.0, dy_ = 0.0;  // FP64 sums
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;  // FP32 Kahan sums
     for (int32_t e = e0; e < e1; e += kChunk) {
@@ -123,10 +127,9 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
     }
     double d2 = 0.0;
     if (want_disp) {
-        const V o = src[v];
         const double ex = static_cast<double>(r.x) - static_cast<double>(o.x);
         const double ey = static_cast<double>(r.y) - static_cast<double>(o.y);
-        d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+        d2 = __fma_rn(ex, ex, __dmul_rn(ey, ey));
     }
     dst[v] = r;
     return d2;
@@ -136,7 +139,7 @@ __device__ __forceinline__ double smooth_vertex(const SweepArgs& a, int32_t v, c
 // (both ping-pong buffers hold them).  Coloured GS: src == dst, every vertex of the range is
 // interior and of one colour, so no two threads touch neighbouring vertices.
 template <bool FP64, bool IN_PLACE, int ARITH>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+__global__ void __launch_bounds__(256, 6) k_sweep(SweepArgs a) {
     if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
     __shared__ double s_recip[kMaxRecipDeg + 1];
     constexpr bool kIntDiv = ARITH == LMS_FP64_ARITH_INT || ARITH == LMS_FP64_ARITH_MIXED2 ||
@@ -278,6 +281,9 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
             double d2 = 0.0;
             if (v < r.y && f0 >= 0) {  // inside the tile and not a boundary vertex
                 const int32_t e0 = f0, e1 = f1 & 0x7fffffff;
+                // old position for the displacement, loaded before the gathers (see smooth_vertex)
+                float2 o = make_float2(0.f, 0.f);
+                if (want_disp) o = src[v];
                 float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
                 for (int32_t e = e0; e < e1; e += CHUNK) {
                     int32_t u[CHUNK];
@@ -298,7 +304,6 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
                 }
                 const float2 q = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
                 if (EXTRAS && want_disp) {
-                    const float2 o = src[v];
                     const double dx = static_cast<double>(__fsub_rn(q.x, o.x)), dy = static_cast<double>(__fsub_rn(q.y, o.y));
                     d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
                 }
@@ -397,20 +402,52 @@ __global__ void k_vertex_quality_exact(int32_t n, const int32_t* __restrict__ vt
 // Per-sweep quality.  Q = (1/n) sum_v (1/n_t(v)) sum_{t in v} q_t = (1/n) sum_t w_t q_t with
 // w_t = sum over t's corners of 1/n_t(corner): one pass over the triangles.  q_t uses the same
 // ratio written as sqrt(min l^2 / max l^2) (one root instead of three).
+//
+// FP64: the squared lengths in FP64; their minimum and maximum by integer compares of the bit patterns
+// (non-negative doubles order like their bits); the root of the ratio from an FP32 seed refined by two
+// Newton steps q <- q - (q^2 max - min) * c in FP64, with c ~ 1/(2 q max) in FP32.  The seed's relative
+// error (under 3e-7) becomes about 1e-13 after one step and a few ulps after two, so the result agrees
+// with sqrt(min / max) to a few ulps while the FP64 unit (GB300's narrow pipe) runs 6 instructions for
+// the root instead of an IEEE division and square root.  Operands outside the ranges the seed handles
+// (a zero or tiny shortest edge, extreme magnitudes) take sqrt(min / max).
+__device__ __forceinline__ bool u64_less(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl) {
+    return ah < bh || (ah == bh && al < bl);
+}
+
 __device__ __forceinline__ double tri_quality_fast(double2 a, double2 b, double2 c) {
     const double e0 = (b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y);
     const double e1 = (c.x - b.x) * (c.x - b.x) + (c.y - b.y) * (c.y - b.y);
     const double e2 = (a.x - c.x) * (a.x - c.x) + (a.y - c.y) * (a.y - c.y);
-    const double lo = fmin(e0, fmin(e1, e2)), hi = fmax(e0, fmax(e1, e2));
-    return hi > 0.0 ? sqrt(lo / hi) : 0.0;
+    uint32_t loh = hi32(e0), lol = lo32(e0), hih = loh, hil = lol;
+    const uint32_t h1 = hi32(e1), l1 = lo32(e1), h2 = hi32(e2), l2 = lo32(e2);
+    if (u64_less(h1, l1, loh, lol)) { loh = h1; lol = l1; }
+    if (u64_less(hih, hil, h1, l1)) { hih = h1; hil = l1; }
+    if (u64_less(h2, l2, loh, lol)) { loh = h2; lol = l2; }
+    if (u64_less(hih, hil, h2, l2)) { hih = h2; hil = l2; }
+    const double lo = from_hilo(loh, lol), hi = from_hilo(hih, hil);
+    const int ehi = static_cast<int>(hih >> 20), elo = static_cast<int>(loh >> 20);
+    if (ehi < 64 || ehi > 1982 || ehi - elo > 126 || elo == 0) return hi > 0.0 ? sqrt(lo / hi) : 0.0;
+    // FP32 images of min and max scaled by 2^-(ehi - 1023) (max in [1, 2)), mantissas truncated
+    const float hf = __int_as_float(static_cast<int>((127u << 23) | ((hih & 0xfffffu) << 3) | (hil >> 29)));
+    const float lf = __int_as_float(static_cast<int>((static_cast<uint32_t>(elo - ehi + 127) << 23) |
+                                                     ((loh & 0xfffffu) << 3) | (lol >> 29)));
+    const float y0 = __fsqrt_rn(__fdiv_rn(lf, hf));       // in [2^-64, 1]
+    const float cf = __frcp_rn(__fmul_rn(2.f, __fmul_rn(y0, hf)));  // in (1/4, 2^63]
+    const uint32_t yb = static_cast<uint32_t>(__float_as_int(y0)), cb = static_cast<uint32_t>(__float_as_int(cf));
+    // exact FP64 copies: y0, and cf * 2^-(ehi - 1023)
+    const double q0 = from_hilo(((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)), yb << 29);
+    const double cq = from_hilo(((static_cast<uint32_t>(static_cast<int>(cb >> 23) + 1919 - ehi) << 20) |
+                                 ((cb & 0x7fffffu) >> 3)), cb << 29);
+    const double q1 = __fma_rn(-__fma_rn(__dmul_rn(q0, q0), hi, -lo), cq, q0);
+    return __fma_rn(-__fma_rn(__dmul_rn(q1, q1), hi, -lo), cq, q1);
 }
 
-__device__ __forceinline__ double tri_quality_fast(float2 a, float2 b, float2 c) {
+__device__ __forceinline__ float tri_quality_fast(float2 a, float2 b, float2 c) {
     const float e0 = (b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y);
     const float e1 = (c.x - b.x) * (c.x - b.x) + (c.y - b.y) * (c.y - b.y);
     const float e2 = (a.x - c.x) * (a.x - c.x) + (a.y - c.y) * (a.y - c.y);
     const float lo = fminf(e0, fminf(e1, e2)), hi = fmaxf(e0, fmaxf(e1, e2));
-    return hi > 0.f ? static_cast<double>(sqrtf(lo / hi)) : 0.0;
+    return hi > 0.f ? sqrtf(lo / hi) : 0.f;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* smem) {
@@ -425,19 +462,37 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return s;  // valid in thread 0
 }
 
-template <typename V>
-__global__ void __launch_bounds__(256) k_quality_partials(int32_t ntri, const int32_t* __restrict__ tri,
-                                                          const V* __restrict__ xy, const double* __restrict__ w,
-                                                          double* __restrict__ partials, const DevState* state) {
+// Per-thread partial sums: FP64 weights and sums for FP64 positions; FP32 weights and Kahan-compensated
+// FP32 sums for FP32 positions (no FP64 instruction per triangle).  Blocks reduce in FP64.
+__global__ void __launch_bounds__(256) k_quality_partials_f64(int32_t ntri, const int32_t* __restrict__ tri,
+                                                              const double2* __restrict__ xy,
+                                                              const double* __restrict__ w,
+                                                              double* __restrict__ partials, const DevState* state) {
     __shared__ double smem[32];
     if (state != nullptr && *reinterpret_cast<const volatile int32_t*>(&state->stop)) return;
     double acc = 0.0;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += gridDim.x * blockDim.x) {
-        const V a = __ldg(xy + __ldg(tri + 3 * t)), b = __ldg(xy + __ldg(tri + 3 * t + 1)),
-                c = __ldg(xy + __ldg(tri + 3 * t + 2));
-        acc += __ldg(w + t) * tri_quality_fast(a, b, c);
+        const double2 a = __ldg(xy + __ldg(tri + 3 * t)), b = __ldg(xy + __ldg(tri + 3 * t + 1)),
+                      c = __ldg(xy + __ldg(tri + 3 * t + 2));
+        acc = __fma_rn(__ldg(w + t), tri_quality_fast(a, b, c), acc);
     }
     const double s = block_sum(acc, smem);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) k_quality_partials_f32(int32_t ntri, const int32_t* __restrict__ tri,
+                                                              const float2* __restrict__ xy,
+                                                              const float* __restrict__ w,
+                                                              double* __restrict__ partials, const DevState* state) {
+    __shared__ double smem[32];
+    if (state != nullptr && *reinterpret_cast<const volatile int32_t*>(&state->stop)) return;
+    float acc = 0.f, comp = 0.f;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += gridDim.x * blockDim.x) {
+        const float2 a = __ldg(xy + __ldg(tri + 3 * t)), b = __ldg(xy + __ldg(tri + 3 * t + 1)),
+                     c = __ldg(xy + __ldg(tri + 3 * t + 2));
+        kahan_add(acc, comp, __fmul_rn(__ldg(w + t), tri_quality_fast(a, b, c)));
+    }
+    const double s = block_sum(static_cast<double>(acc) - static_cast<double>(comp), smem);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -712,14 +767,14 @@ cudaError_t launch_vertex_quality_exact(int32_t n, const int32_t* vt_ptr, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_quality_partials(int precision, int32_t ntri, const int32_t* tri, const void* xy, const double* w,
+cudaError_t launch_quality_partials(int precision, int32_t ntri, const int32_t* tri, const void* xy, const void* w,
                                     double* partials, const DevState* state, cudaStream_t stream) {
     if (precision == LMS_FP64)
-        k_quality_partials<double2><<<kQualityBlocks, 256, 0, stream>>>(
-            ntri, tri, static_cast<const double2*>(xy), w, partials, state);
+        k_quality_partials_f64<<<kQualityBlocks, 256, 0, stream>>>(
+            ntri, tri, static_cast<const double2*>(xy), static_cast<const double*>(w), partials, state);
     else
-        k_quality_partials<float2><<<kQualityBlocks, 256, 0, stream>>>(
-            ntri, tri, static_cast<const float2*>(xy), w, partials, state);
+        k_quality_partials_f32<<<kQualityBlocks, 256, 0, stream>>>(
+            ntri, tri, static_cast<const float2*>(xy), static_cast<const float*>(w), partials, state);
     return cudaGetLastError();
 }
 
