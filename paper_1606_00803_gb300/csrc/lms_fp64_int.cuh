@@ -10,6 +10,8 @@
 //                             sum or difference of the two integers is exact (at most 63 bits), and it is
 //                             rounded once.  Otherwise (zero or subnormal operands, the top binade, a wider
 //                             exponent gap, a subnormal result) the FP64 unit adds.
+//   root_of_ratio(lo, hi)     sqrt(lo / hi) within a few ulps for the per-sweep quality: an FP32 seed and
+//                             two FP64 Newton steps (6 FP64 instructions instead of a division and a root).
 //   div_rn_int(s, d, magic)   RN(s / d) for an integer 1 <= d <= 64: N = significand * 2^11 is divided by d
 //                             with a multiply-high by floor((2^64 - 1) / d) (words magic[2d], magic[2d+1])
 //                             and at most one correction (division by invariant integers, Granlund & Montgomery, PLDI 1994),
@@ -20,6 +22,7 @@
 // excluded cases.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -201,6 +204,90 @@ LMS_HD bool div_rn_int(double s, int d, const uint32_t* magic, double* q) {
     if (e <= 0) return false;
     *q = round_pack(qh, ql, p, e, r != 0u, h & 0x80000000u);
     return true;
+}
+
+// ---- sqrt(lo / hi) for the per-sweep quality: an FP32 seed refined by two FP64 Newton steps
+
+LMS_HD float f32_from_bits(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(static_cast<int>(u));
+#else
+    float x;
+    std::memcpy(&x, &u, sizeof x);
+    return x;
+#endif
+}
+
+LMS_HD uint32_t f32_bits(float x) {
+#ifdef __CUDA_ARCH__
+    return static_cast<uint32_t>(__float_as_int(x));
+#else
+    uint32_t u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+#endif
+}
+
+// one IEEE operation each, rounded to nearest
+LMS_HD float f32_sqrt_of_ratio(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsqrt_rn(__fdiv_rn(a, b));
+#else
+    volatile float q = a / b;
+    return std::sqrt(static_cast<float>(q));
+#endif
+}
+
+LMS_HD float f32_rcp_twice_product(float y, float h) {
+#ifdef __CUDA_ARCH__
+    return __frcp_rn(__fmul_rn(2.f, __fmul_rn(y, h)));
+#else
+    volatile float p = y * h;
+    volatile float p2 = 2.f * p;
+    return 1.f / static_cast<float>(p2);
+#endif
+}
+
+LMS_HD double f64_newton_step(double q, double lo, double hi, double c) {  // q - (q*q*hi - lo) * c
+#ifdef __CUDA_ARCH__
+    return __fma_rn(-__fma_rn(__dmul_rn(q, q), hi, -lo), c, q);
+#else
+    volatile double qq = q * q;
+    return std::fma(-std::fma(static_cast<double>(qq), hi, -lo), c, q);
+#endif
+}
+
+LMS_HD double root_of_ratio_fpu(double lo, double hi) {
+    if (!(hi > 0.0)) return 0.0;
+#ifdef __CUDA_ARCH__
+    return sqrt(lo / hi);
+#else
+    volatile double r = lo / hi;
+    return std::sqrt(static_cast<double>(r));
+#endif
+}
+
+// sqrt(lo / hi) for 0 <= lo <= hi (the shortest and longest squared edge of a triangle), within a few
+// ulps.  The seed: FP32 images of lo and hi scaled by 2^-(ehi - 1023) so that hi lies in [1, 2)
+// (mantissas truncated to 23 bits), y0 = sqrt(lo' / hi') and c = 1 / (2 y0 hi') in FP32 (relative error
+// under 3e-7), both widened exactly to FP64 through their bit patterns (c rescaled by 2^-(ehi - 1023)).
+// Two Newton steps q <- q - (q^2 hi - lo) c square that error (about 1e-13 after one step, a few ulps
+// after two).  lo zero or subnormal, hi outside [2^-959, 2^959], or lo/hi below 2^-126 take the FPU.
+LMS_HD double root_of_ratio(double lo, double hi) {
+    const uint32_t hih = hi32(hi), hil = lo32(hi), loh = hi32(lo), lol = lo32(lo);
+    const int ehi = static_cast<int>(hih >> 20), elo = static_cast<int>(loh >> 20);
+    if (ehi < 64 || ehi > 1982 || ehi - elo > 126 || elo == 0) return root_of_ratio_fpu(lo, hi);
+    const float hf = f32_from_bits((127u << 23) | ((hih & 0xfffffu) << 3) | (hil >> 29));
+    const float lf = f32_from_bits((static_cast<uint32_t>(elo - ehi + 127) << 23) | ((loh & 0xfffffu) << 3) |
+                                   (lol >> 29));
+    const float y0 = f32_sqrt_of_ratio(lf, hf);   // in [2^-64, 1]
+    const float cf = f32_rcp_twice_product(y0, hf);  // in (1/4, 2^63]
+    const uint32_t yb = f32_bits(y0), cb = f32_bits(cf);
+    const double q0 = from_hilo((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3), yb << 29);
+    const double c = from_hilo((static_cast<uint32_t>(static_cast<int>(cb >> 23) + 1919 - ehi) << 20) |
+                                   ((cb & 0x7fffffu) >> 3),
+                               cb << 29);
+    return f64_newton_step(f64_newton_step(q0, lo, hi, c), lo, hi, c);
 }
 
 }  // namespace dev

@@ -424,22 +424,7 @@ __device__ __forceinline__ double tri_quality_fast(double2 a, double2 b, double2
     if (u64_less(hih, hil, h1, l1)) { hih = h1; hil = l1; }
     if (u64_less(h2, l2, loh, lol)) { loh = h2; lol = l2; }
     if (u64_less(hih, hil, h2, l2)) { hih = h2; hil = l2; }
-    const double lo = from_hilo(loh, lol), hi = from_hilo(hih, hil);
-    const int ehi = static_cast<int>(hih >> 20), elo = static_cast<int>(loh >> 20);
-    if (ehi < 64 || ehi > 1982 || ehi - elo > 126 || elo == 0) return hi > 0.0 ? sqrt(lo / hi) : 0.0;
-    // FP32 images of min and max scaled by 2^-(ehi - 1023) (max in [1, 2)), mantissas truncated
-    const float hf = __int_as_float(static_cast<int>((127u << 23) | ((hih & 0xfffffu) << 3) | (hil >> 29)));
-    const float lf = __int_as_float(static_cast<int>((static_cast<uint32_t>(elo - ehi + 127) << 23) |
-                                                     ((loh & 0xfffffu) << 3) | (lol >> 29)));
-    const float y0 = __fsqrt_rn(__fdiv_rn(lf, hf));       // in [2^-64, 1]
-    const float cf = __frcp_rn(__fmul_rn(2.f, __fmul_rn(y0, hf)));  // in (1/4, 2^63]
-    const uint32_t yb = static_cast<uint32_t>(__float_as_int(y0)), cb = static_cast<uint32_t>(__float_as_int(cf));
-    // exact FP64 copies: y0, and cf * 2^-(ehi - 1023)
-    const double q0 = from_hilo(((((yb >> 23) + 896u) << 20) | ((yb & 0x7fffffu) >> 3)), yb << 29);
-    const double cq = from_hilo(((static_cast<uint32_t>(static_cast<int>(cb >> 23) + 1919 - ehi) << 20) |
-                                 ((cb & 0x7fffffu) >> 3)), cb << 29);
-    const double q1 = __fma_rn(-__fma_rn(__dmul_rn(q0, q0), hi, -lo), cq, q0);
-    return __fma_rn(-__fma_rn(__dmul_rn(q1, q1), hi, -lo), cq, q1);
+    return root_of_ratio(from_hilo(loh, lol), from_hilo(hih, hil));
 }
 
 __device__ __forceinline__ float tri_quality_fast(float2 a, float2 b, float2 c) {

@@ -1,6 +1,7 @@
 """The FP64 sweep's integer-pipe arithmetic (add_rn_int and div_rn_int in lms_fp64_int.cuh), compiled for
 the host from the same header, against IEEE 754 binary64 addition and division rounded to nearest (the
-host FPU through numpy).
+host FPU through numpy); and the per-sweep quality's root of a ratio (root_of_ratio: FP32 seed, two FP64
+Newton steps) against sqrt(lo / hi).
 
 The cases are chosen so that a slip anywhere in the routines fails one of them: ties at every exponent
 distance around the 53-bit boundary (round-half-even), every alignment the integer path takes and the
@@ -28,6 +29,9 @@ extern "C" void plus_zero_batch(long n, const double* a, double* s) {
     for (long i = 0; i < n; ++i) s[i] = lms::dev::plus_zero(a[i]);
 }
 // q[i] = s[i] / d[i] by div_rn_int; declined[i] = 1 where it hands the division back (q[i] untouched)
+extern "C" void root_batch(long n, const double* lo, const double* hi, double* r) {
+    for (long i = 0; i < n; ++i) r[i] = lms::dev::root_of_ratio(lo[i], hi[i]);
+}
 extern "C" void div_batch(long n, const double* s, const int* d, double* q, unsigned char* declined) {
     uint32_t magic[130] = {0};
     for (int i = 1; i <= 64; ++i) lms::dev::div_magic(i, magic + 2 * i, magic + 2 * i + 1);
@@ -51,6 +55,7 @@ def lib(tmp_path_factory):
     L.add_batch.argtypes = [ctypes.c_long, P, P, P]
     L.plus_zero_batch.argtypes = [ctypes.c_long, P, P]
     L.div_batch.argtypes = [ctypes.c_long, P, P, P, P]
+    L.root_batch.argtypes = [ctypes.c_long, P, P, P]
     return L
 
 
@@ -231,3 +236,33 @@ def test_division_hand_offs(lib):
     s2, d2 = np.meshgrid(s, np.arange(1, 65, dtype=np.int32))
     declined = assert_div_bitwise(lib, s2.ravel(), d2.ravel())
     assert declined[(s2.ravel() == 0)].all()
+
+
+def emul_root(L, lo, hi):
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    r = np.empty_like(lo)
+    L.root_batch(len(lo), lo.ctypes.data, hi.ctypes.data, r.ctypes.data)
+    return r
+
+
+def test_root_of_ratio_within_two_ulps(lib):
+    # squared edge lengths of every magnitude the seed handles, ratios down to 2^-126
+    rng = np.random.default_rng(8)
+    n = 600_000
+    hi = rng.uniform(1, 2, n) * np.exp2(rng.integers(-950, 950, n).astype(np.float64))
+    lo = np.minimum(hi * np.exp2(-rng.uniform(0, 125, n)) * rng.uniform(0.5, 1, n), hi)
+    lo[:1000] = hi[:1000]                            # equilateral: ratio exactly 1
+    lo[1000:2000] = hi[1000:2000] * 0.25             # exact roots
+    got = emul_root(lib, lo, hi)
+    want = np.sqrt(lo / hi)
+    assert np.all(np.abs(got - want) <= 2 * np.spacing(want))
+
+
+def test_root_of_ratio_hand_offs_are_the_fpu_result(lib):
+    tiny = np.finfo(np.float64).tiny
+    hi = np.array([0.0, 1.0, 1.0, 1e-300, 1e300, 1.0, 3.0, 5e-324])
+    lo = np.array([0.0, 0.0, 5e-324, 1e-301, 1e299, 2.0 ** -130, tiny, 5e-324])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        want = np.where(hi > 0, np.sqrt(lo / hi), 0.0)
+    assert np.array_equal(emul_root(lib, lo, hi), want)
