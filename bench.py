@@ -538,7 +538,7 @@ def run_ours(args, dist):
             arithmetic="IEEE FP64, bit-identical to the oracle; divisions and every third add of a row on 32-bit "
                        "integer instructions, the other adds on the FP64 unit (LMS_FP64_ARITH_MIXED3)",
             roofline=dict(bound="alu", achieved=rdr["fp64_ops_per_s"] / 1e9, peak=2 * 152 * 2.07,
-                          unit="G FP64 instr/s", frac=round(rdr["fp64_ops_per_s"] / 1e9 / (2 * 152 * 2.07), 3),
+                          unit="G IEEE FP64 ops/s", frac=round(rdr["fp64_ops_per_s"] / 1e9 / (2 * 152 * 2.07), 3),
                           peak_note=FP64_OPS_PEAK_NOTE),
             hbm_frac=rdr["hbm_frac"])
         extras["stopping_rule"] = stopping_table()
