@@ -74,6 +74,8 @@ def _lib():
             "or_relabel": [_I32, _P_I32, _P_I32, _P_I32, _P_I32, _P_I32],
             "or_color_greedy": [_I32, _P_I32, _P_I32, _P_U8, _P_I32, _P_I32, _P_I32],
             "or_color_sequence": [_I32, _P_U8, _P_I32, _P_I32, _I32, _P_I32, _P_I32],
+            "or_block_sequence": [_I32, _P_I32, _P_I32, _P_U8, _P_I32, _P_I32, _I32, _I32, _P_I32, _P_I32,
+                                  _P_I32, _P_I32],
             "or_order_rbfs": [_I32, _P_I32, _P_I32, _P_I32],
             "or_order_brdr": [_I32, _P_I32, _P_I32, _P_U8, _P_F64, _I32, _P_I32],
             "or_access_trace": [_I32, _P_I32, _P_I32, _P_U8, _I32, _P_I32, _I32, _P_I32, _P_I64],
@@ -254,6 +256,28 @@ def color_sequence(is_boundary, new_to_old, colour, ncolours):
     _check(_lib().or_color_sequence(n, _p(bnd, _P_U8), _p(p, _P_I32), _p(colour, _P_I32), ncolours,
                                     _p(seq, _P_I32), ctypes.byref(m)), "color_sequence")
     return seq[: m.value]
+
+
+def block_sequence(row_ptr, col_idx, is_boundary, new_to_old, colour, ncolours, tile):
+    """Block order of the in-place sweep: (tile colour, tile, vertex colour, storage position).  Returns
+    (seq of original ids, tile colours, number of tile colours)."""
+    rp, ci, bnd, p, colour = _i32(row_ptr), _i32(col_idx), _u8(is_boundary), _i32(new_to_old), _i32(colour)
+    n = len(rp) - 1
+    ntiles = (n + tile - 1) // tile
+    tc, nt = np.empty(ntiles, np.int32), ctypes.c_int32()
+    seq, m = np.empty(n, np.int32), ctypes.c_int32()
+    _check(_lib().or_block_sequence(n, _p(rp, _P_I32), _p(ci, _P_I32), _p(bnd, _P_U8), _p(p, _P_I32),
+                                    _p(colour, _P_I32), ncolours, tile, _p(tc, _P_I32), ctypes.byref(nt),
+                                    _p(seq, _P_I32), ctypes.byref(m)), "block_sequence")
+    return seq[: m.value], tc, nt.value
+
+
+def block_gs_smooth(mesh, new_to_old, tile, iters, tol=-1.0):
+    """Block Gauss-Seidel reference: in-place sweeps in block order over the first-fit colouring."""
+    colour, nc = color_greedy(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], new_to_old)
+    seq, _, _ = block_sequence(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], new_to_old, colour, nc, tile)
+    return smooth(mesh["row_ptr"], mesh["col_idx"], mesh["is_boundary"], mesh["xy"], iters, mode=INPLACE, seq=seq,
+                  tri=mesh["tri"] if tol >= 0 else None, tol=tol)
 
 
 def gs_smooth(mesh, new_to_old, iters, tol=-1.0):

@@ -36,6 +36,14 @@
  *   or_order_brdr - a blocked variant of Algorithm 2 that is not in the paper:
  *       the BFS order cut into blocks of consecutive positions, Algorithm 2
  *       applied to each block's own subgraph, blocks kept in BFS order.
+ *   or_block_sequence - an order for Algorithm 1's in-place sweep that is not
+ *       in the paper: the storage order cut into tiles of consecutive
+ *       positions, the tiles coloured first-fit (ascending tile index) so that
+ *       no two tiles of one colour share an edge between interior vertices,
+ *       and the interior vertices visited by (tile colour, tile, vertex
+ *       colour, storage position).  Tiles of one colour, and the vertices of
+ *       one colour inside a tile, are independent, so a parallel sweep that
+ *       runs them together equals the sequential sweep in this order.
  *   or_access_trace / or_reuse_distances / or_quantile - Section 2.2's reuse
  *       distance over the data accesses of one sweep (Fig. 3: a vertex, then
  *       its neighbours), and the quantiles of Table 2 (the X quantile is the
@@ -458,6 +466,68 @@ int or_color_sequence(int32_t n, const uint8_t* is_boundary, const int32_t* new_
             int32_t v = new_to_old[k];
             if (!is_boundary[v] && colour[v] == c) seq[m++] = v;
         }
+    *nseq = m;
+    return OR_OK;
+}
+
+/*
+ * Block order of the in-place sweep (see the file header).  Storage position k
+ * lies in tile k / tile; colour[] is a proper colouring of the interior
+ * vertices by original id (-1 = boundary), e.g. or_color_greedy's.  Outputs:
+ * tile_colour[ceil(n / tile)] (tiles without interior vertices get colour 0),
+ * *ntile_colours, and seq (original ids of the interior vertices in block
+ * order) with its length in *nseq.
+ */
+int or_block_sequence(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                      const int32_t* new_to_old, const int32_t* colour, int32_t ncolours, int32_t tile,
+                      int32_t* tile_colour, int32_t* ntile_colours, int32_t* seq, int32_t* nseq) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !new_to_old || !colour || ncolours < 0 || tile < 1 ||
+        !tile_colour || !ntile_colours || !seq || !nseq)
+        return OR_ERR_ARG;
+    const int32_t ntiles = (int32_t)(((int64_t)n + tile - 1) / tile);
+    int32_t* pos = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t* used = (uint8_t*)calloc((size_t)ntiles + 1, 1);
+    if (!pos || !used) {
+        free(pos);
+        free(used);
+        return OR_ERR_OOM;
+    }
+    for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
+    for (int32_t t = 0; t < ntiles; ++t) tile_colour[t] = -1;
+    int32_t nt = 0;
+    for (int32_t t = 0; t < ntiles; ++t) {
+        /* colours of the already coloured tiles that share an interior-interior edge with tile t */
+        memset(used, 0, (size_t)ntiles + 1);
+        const int32_t k1 = (int32_t)((int64_t)(t + 1) * tile < n ? (t + 1) * tile : n);
+        for (int32_t k = t * tile; k < k1; ++k) {
+            const int32_t v = new_to_old[k];
+            if (is_boundary[v]) continue;
+            for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                const int32_t u = col_idx[e];
+                if (is_boundary[u]) continue;
+                const int32_t tu = pos[u] / tile;
+                if (tu != t && tile_colour[tu] >= 0) used[tile_colour[tu]] = 1;
+            }
+        }
+        int32_t c = 0;
+        while (used[c]) ++c;
+        tile_colour[t] = c;
+        if (c + 1 > nt) nt = c + 1;
+    }
+    int32_t m = 0;
+    for (int32_t tc = 0; tc < nt; ++tc)
+        for (int32_t t = 0; t < ntiles; ++t) {
+            if (tile_colour[t] != tc) continue;
+            const int32_t k1 = (int32_t)((int64_t)(t + 1) * tile < n ? (t + 1) * tile : n);
+            for (int32_t c = 0; c < ncolours; ++c)
+                for (int32_t k = t * tile; k < k1; ++k) {
+                    const int32_t v = new_to_old[k];
+                    if (!is_boundary[v] && colour[v] == c) seq[m++] = v;
+                }
+        }
+    free(pos);
+    free(used);
+    *ntile_colours = nt;
     *nseq = m;
     return OR_OK;
 }
