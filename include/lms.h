@@ -179,6 +179,20 @@ int lms_color_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours);
 
 /*
+ * Block order of Algorithm 1's in-place sweep (not in the paper; the sequential form of a block
+ * Gauss-Seidel): the storage order new_to_old cut into tiles of `tile` consecutive positions; tiles
+ * coloured first-fit in ascending tile index so that no two tiles of one colour share an edge between
+ * interior vertices (tile_colour: [ceil(n / tile)] output; tiles without interior vertices get 0;
+ * *ntile_colours the count); order: [n] output receiving the interior vertices (original ids) by
+ * (tile colour, tile, colour of lms_color_host's colouring, storage position), *n_order their count.
+ * Tiles of one colour, and one colour's vertices inside a tile, are independent, so sweeping them at
+ * the same time equals the in-place sweep in this order.  LMS_ERR_ARG, LMS_ERR_OOM.  [host]
+ */
+int lms_block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
+                    int32_t* order, int32_t* n_order);
+
+/*
  * Create a smoothing handle: validates the mesh (as lms_validate), copies it
  * to the device and stores the coordinates in `precision`.  The initial
  * ordering is LMS_ORI.  tri may be NULL (ntri = 0); quality, LMS_RDR and the

@@ -83,6 +83,7 @@ _SIGS = {
     "lms_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
     "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
+    "lms_block_order": ([_I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "lms_set_fp64_arith": ([_P, _I32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
@@ -280,6 +281,21 @@ def debug_checks(reset=False):
 def selftest_timeout(wait_us=2000):
     """lms_selftest_timeout: status of a bounded device wait that is made to expire (LMS_ERR_TIMEOUT = -7)."""
     return _lib().lms_selftest_timeout(int(wait_us))
+
+
+def block_order(row_ptr, col_idx, is_boundary, new_to_old, tile):
+    """Block order of the in-place sweep (lms_block_order): (order of original ids, tile colours, count)."""
+    rp, ci = _arr(row_ptr, np.int32), _arr(col_idx, np.int32)
+    bnd, p = _arr(is_boundary, np.uint8), _arr(new_to_old, np.int32)
+    n = len(rp) - 1
+    if int(tile) < 1:
+        raise ValueError("tile must be positive")
+    tc = np.empty((n + int(tile) - 1) // int(tile), np.int32)
+    order = np.empty(n, np.int32)
+    nt, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().lms_block_order(n, _ptr(rp), _ptr(ci), _ptr(bnd), _ptr(p), int(tile), _ptr(tc), ctypes.byref(nt),
+                                  _ptr(order), ctypes.byref(m)), "lms_block_order")
+    return order[: m.value], tc, nt.value
 
 
 def selftest_add64(a, b):

@@ -452,6 +452,70 @@ int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, c
     return LMS_OK;
 }
 
+// Block order of the in-place sweep for a block Gauss-Seidel: tiles of `tile` consecutive storage
+// positions, coloured first-fit in ascending tile index so that no two tiles of a colour share an edge
+// between interior vertices; interior vertices ordered by (tile colour, tile, vertex colour of the
+// first-fit vertex colouring, storage position).  Tiles of one colour, and one colour's vertices inside a
+// tile, are independent.  Tile adjacency is gathered per tile and deduplicated with a stamp array;
+// the order is two stable counting sorts (tiles by colour, then each tile's vertices by colour).
+int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
+                int32_t* order, int32_t* n_order) {
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !new_to_old || tile < 1 || !tile_colour ||
+        !ntile_colours || !order || !n_order)
+        return LMS_ERR_ARG;
+    std::vector<int32_t> colour(n);
+    int32_t nc = 0;
+    if (int rc = colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour.data(), &nc)) return rc;
+    std::vector<int32_t> pos(n);
+    for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
+    const int32_t ntiles = static_cast<int32_t>((static_cast<int64_t>(n) + tile - 1) / tile);
+    // first-fit tile colours; stamp[c] == t + 1 marks colour c as taken by a neighbour of tile t
+    std::vector<int32_t> stamp(static_cast<size_t>(ntiles) + 1, 0);
+    int32_t nt = 0;
+    for (int32_t t = 0; t < ntiles; ++t) {
+        const int32_t k0 = t * tile, k1 = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(k0) + tile, n));
+        for (int32_t k = k0; k < k1; ++k) {
+            const int32_t v = new_to_old[k];
+            if (is_boundary[v]) continue;
+            for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                const int32_t u = col_idx[e];
+                if (is_boundary[u]) continue;
+                const int32_t tu = pos[u] / tile;
+                if (tu < t) stamp[tile_colour[tu]] = t + 1;  // tiles above t are not coloured yet
+            }
+        }
+        int32_t c = 0;
+        while (stamp[c] == t + 1) ++c;
+        tile_colour[t] = c;
+        nt = std::max(nt, c + 1);
+    }
+    // tiles by colour (stable), then each tile's interior vertices by colour (stable)
+    std::vector<int32_t> tile_start(static_cast<size_t>(nt) + 1, 0), tiles(ntiles);
+    for (int32_t t = 0; t < ntiles; ++t) ++tile_start[tile_colour[t] + 1];
+    for (int32_t c = 0; c < nt; ++c) tile_start[c + 1] += tile_start[c];
+    for (int32_t t = 0; t < ntiles; ++t) tiles[tile_start[tile_colour[t]]++] = t;
+    std::vector<int32_t> count(static_cast<size_t>(nc) + 1);
+    int32_t m = 0;
+    for (int32_t t : tiles) {
+        const int32_t k0 = t * tile, k1 = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(k0) + tile, n));
+        std::fill(count.begin(), count.end(), 0);
+        for (int32_t k = k0; k < k1; ++k) {
+            const int32_t v = new_to_old[k];
+            if (!is_boundary[v]) ++count[colour[v] + 1];
+        }
+        for (int32_t c = 0; c < nc; ++c) count[c + 1] += count[c];
+        for (int32_t k = k0; k < k1; ++k) {
+            const int32_t v = new_to_old[k];
+            if (!is_boundary[v]) order[m + count[colour[v]]++] = v;
+        }
+        m += count[nc];
+    }
+    *ntile_colours = nt;
+    *n_order = m;
+    return LMS_OK;
+}
+
 }  // namespace lms
 
 extern "C" {
@@ -484,6 +548,17 @@ int lms_order_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
 int lms_color_host(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                    const int32_t* new_to_old, int32_t* colour, int32_t* ncolours) {
     return lms::colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour, ncolours);
+}
+
+int lms_block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                    const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
+                    int32_t* order, int32_t* n_order) {
+    try {
+        return lms::block_order(n, row_ptr, col_idx, is_boundary, new_to_old, tile, tile_colour, ntile_colours,
+                                order, n_order);
+    } catch (const std::bad_alloc&) {
+        return LMS_ERR_OOM;
+    }
 }
 
 int lms_reuse_profile(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,

@@ -27,6 +27,11 @@ int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
 int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                     const int32_t* new_to_old, int32_t* colour, int32_t* ncolours);
 
+// Block order of the in-place sweep (see lms_block_order in lms.h).
+int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
+                int32_t* order, int32_t* n_order);
+
 // Set the message reported with LMS_ERR_CUDA and friends (thread-local).
 void set_error_detail(const std::string& s);
 const std::string& error_detail();

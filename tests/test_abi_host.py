@@ -1,6 +1,7 @@
 """C ABI of liblms without a GPU: the library loads, exports every entry point
 that include/lms.h declares, and its host logic (validation, the four orderings
 and the colouring) matches the FP64 oracle bit for bit."""
+import ctypes
 import os
 import re
 import subprocess
@@ -211,3 +212,32 @@ def test_binding_declares_a_signature_for_every_entry_point():
     # an entry point without argtypes would pass 64-bit pointers as 32-bit ints
     missing = [n for n in declared_entry_points() if n not in lms._SIGS]
     assert not missing, missing
+
+
+@pytest.mark.parametrize("ordering", [oracle.ORI, oracle.BFS, oracle.RDR, oracle.RANDOM])
+def test_block_order_host_equals_oracle(ordering):
+    # library (stamp-array tile colouring, counting sorts) against the oracle's plain loops
+    for m in (meshgen.workload(1, side=33), meshgen.workload(2, side=21)):
+        p = oracle.order(m, ordering, seed=9)
+        colour, nc = oracle.color_greedy(m["row_ptr"], m["col_idx"], m["is_boundary"], p)
+        for tile in (1, 2, 5, 128, 700, m["n"], m["n"] + 3):
+            want, tcw, ntw = oracle.block_sequence(m["row_ptr"], m["col_idx"], m["is_boundary"], p, colour, nc, tile)
+            got, tcg, ntg = lms.block_order(m["row_ptr"], m["col_idx"], m["is_boundary"], p, tile)
+            assert np.array_equal(got, want) and np.array_equal(tcg, tcw) and ntg == ntw
+
+
+def test_block_order_rejects_bad_arguments():
+    m = meshgen.workload(0)
+    p = np.arange(m["n"], dtype=np.int32)
+    with pytest.raises(ValueError):
+        lms.block_order(m["row_ptr"], m["col_idx"], m["is_boundary"], p, 0)
+    out = np.empty(m["n"], np.int32)
+    nt, k = ctypes.c_int32(), ctypes.c_int32()
+    rc = lms._lib().lms_block_order(m["n"], m["row_ptr"].ctypes.data, m["col_idx"].ctypes.data,
+                                    m["is_boundary"].ctypes.data, p.ctypes.data, -4, out.ctypes.data,
+                                    ctypes.byref(nt), out.ctypes.data, ctypes.byref(k))
+    assert rc == -1  # LMS_ERR_ARG
+    rc = lms._lib().lms_block_order(m["n"], None, m["col_idx"].ctypes.data, m["is_boundary"].ctypes.data,
+                                    p.ctypes.data, 8, out.ctypes.data, ctypes.byref(nt), out.ctypes.data,
+                                    ctypes.byref(k))
+    assert rc == -1
