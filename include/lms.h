@@ -85,6 +85,11 @@ extern "C" {
                                 block (lms_set_inplace_split); neighbours are read as they are at that
                                 moment, so results depend on timing - except with one thread, which is
                                 the sequential in-place sweep in storage order */
+#define LMS_BLOCK_GS 3 /* not in the paper: block Gauss-Seidel - Algorithm 1 in place in the block order
+                          of lms_block_order (tiles of lms_set_block_tile consecutive positions of the
+                          ordering), tiles of one tile colour swept at the same time, colour groups
+                          inside a tile one after another; deterministic, equal to the sequential
+                          in-place sweep in that order */
 
 /* sweep kernels */
 #define LMS_KERNEL_DIRECT 0 /* one thread per vertex; CSR and positions loaded through L1; rows read `chunk`
@@ -193,6 +198,16 @@ int lms_block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, c
                     int32_t* order, int32_t* n_order);
 
 /*
+ * Diagnostic of the LMS_BLOCK_GS tables: builds them for storage order new_to_old and tile as a handle
+ * does, and walks them in the device sweep's launch order (tile colour, tile, colour group, table
+ * order), writing the visited interior vertices (original ids) to seq ([n]), their count to *nseq and
+ * the number of launches of one sweep to *n_launches.  Equals lms_block_order's order.  LMS_ERR_ARG,
+ * LMS_ERR_OOM.  [host]
+ */
+int lms_block_walk(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const int32_t* new_to_old, int32_t tile, int32_t* seq, int32_t* nseq, int32_t* n_launches);
+
+/*
  * Create a smoothing handle: validates the mesh (as lms_validate), copies it
  * to the device and stores the coordinates in `precision`.  The initial
  * ordering is LMS_ORI.  tri may be NULL (ntri = 0); quality, LMS_RDR and the
@@ -236,6 +251,12 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
  * beyond FP32 rounding.
  */
 int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
+
+/* Tile of LMS_BLOCK_GS sweeps in storage positions (tile >= 1), or 0 to choose it by mesh size (about
+   three CTAs per SM for each tile colour, within 128..4096).  The sweep's result depends on the tile
+   (it fixes the order).  lms_get_block_tile returns the tile the next sweep uses.  [host] */
+int lms_set_block_tile(lms_handle h, int32_t tile);
+int lms_get_block_tile(lms_handle h, int32_t* tile);
 
 /* Where the arithmetic of FP64 Jacobi and coloured GS sweeps (Eq. 1) runs: LMS_FP64_ARITH_* (default
    LMS_FP64_ARITH_MIXED3).  GB300 executes FP64 instructions at a little over one lane per clock per SM and

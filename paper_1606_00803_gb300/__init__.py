@@ -25,7 +25,7 @@ FP64, FP32 = 0, 1
 KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
 ORI, RANDOM, BFS, RDR, RBFS, BRDR = 0, 1, 2, 3, 4, 5
 BRDR_BLOCK = 4096  # LMS_BRDR_BLOCK
-JACOBI, COLORED_GS, INPLACE_STATIC = 0, 1, 2
+JACOBI, COLORED_GS, INPLACE_STATIC, BLOCK_GS = 0, 1, 2, 3
 REUSE_DISTINCT, REUSE_ACCESSES = 0, 1
 FP64_ARITH_FPU, FP64_ARITH_INT_ADDS, FP64_ARITH_INT, FP64_ARITH_MIXED2, FP64_ARITH_MIXED3 = 0, 1, 2, 3, 4
 ORDERINGS = {"ori": ORI, "random": RANDOM, "bfs": BFS, "rdr": RDR, "rbfs": RBFS, "brdr": BRDR}
@@ -84,7 +84,10 @@ _SIGS = {
     "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
     "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
     "lms_block_order": ([_I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "lms_block_walk": ([_I32, _P, _P, _P, _P, _I32, _P, _PI32, _PI32], ctypes.c_int),
     "lms_set_fp64_arith": ([_P, _I32], ctypes.c_int),
+    "lms_set_block_tile": ([_P, _I32], ctypes.c_int),
+    "lms_get_block_tile": ([_P, _PI32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_add64": ([_I32, _P, _P, _P], ctypes.c_int),
@@ -298,6 +301,18 @@ def block_order(row_ptr, col_idx, is_boundary, new_to_old, tile):
     return order[: m.value], tc, nt.value
 
 
+def block_walk(row_ptr, col_idx, is_boundary, new_to_old, tile):
+    """The BLOCK_GS tables walked in launch order (lms_block_walk): (visited original ids, launches)."""
+    rp, ci = _arr(row_ptr, np.int32), _arr(col_idx, np.int32)
+    bnd, p = _arr(is_boundary, np.uint8), _arr(new_to_old, np.int32)
+    n = len(rp) - 1
+    seq = np.empty(n, np.int32)
+    m, launches = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().lms_block_walk(n, _ptr(rp), _ptr(ci), _ptr(bnd), _ptr(p), int(tile), _ptr(seq), ctypes.byref(m),
+                                 ctypes.byref(launches)), "lms_block_walk")
+    return seq[: m.value], launches.value
+
+
 def selftest_add64(a, b):
     """Device sums a+b by the FP64 sweep's integer-pipe addition (lms_selftest_add64)."""
     a, b = _arr(a, np.float64), _arr(b, np.float64)
@@ -408,6 +423,16 @@ class Mesh:
     def set_inplace_split(self, threads):
         """GPU threads of INPLACE_STATIC sweeps (0 = default, 1 = sequential Algorithm 1)."""
         _check(_lib().lms_set_inplace_split(self._handle(), int(threads)), "lms_set_inplace_split")
+
+    def set_block_tile(self, tile):
+        """Tile (storage positions) of BLOCK_GS sweeps; 0 = by mesh size."""
+        _check(_lib().lms_set_block_tile(self._handle(), int(tile)), "lms_set_block_tile")
+
+    def block_tile(self):
+        """Tile the next BLOCK_GS sweep uses."""
+        t = ctypes.c_int32()
+        _check(_lib().lms_get_block_tile(self._handle(), ctypes.byref(t)), "lms_get_block_tile")
+        return t.value
 
     def set_fp64_arith(self, mode):
         """Where FP64 sums and means run: FP64_ARITH_* (every mode gives the same results)."""

@@ -283,6 +283,15 @@ struct lms_mesh_s {
     double last_disp = NAN, last_ms = NAN, q_first = NAN, q_last = NAN;
     double reorder_ms[2] = {NAN, NAN};  // last lms_reorder: ordering, relabelled layout
     int32_t inplace_threads = 0;        // LMS_INPLACE_STATIC split (0: one thread per resident slot)
+    // LMS_BLOCK_GS tables for the ordering layout (rebuilt after a reorder or a tile change)
+    int32_t block_tile_req = 0;         // requested tile (0: by mesh size)
+    int32_t block_tile = 0;             // tile of the current tables
+    bool block_valid = false;
+    int32_t block_ncolours = 0;         // vertex colours (group slots per tile)
+    std::vector<int32_t> block_tc_ofs;  // tile colour c: listed tiles [ofs[c], ofs[c+1])
+    int32_t* d_blk_verts = nullptr;
+    int32_t* d_blk_groups = nullptr;
+    int64_t blk_verts_cap = 0, blk_groups_cap = 0;
     int32_t fp64_arith = LMS_FP64_ARITH_MIXED3;  // where FP64 sums and means run (fastest on GB300)
 
     ~lms_mesh_s() {
@@ -510,7 +519,10 @@ int ensure_queue(lms_mesh_s* h, int32_t slots) {
     return LMS_OK;
 }
 
-int launches_per_sweep(lms_mesh_s* h, int mode) { return mode == LMS_COLORED_GS ? h->ncolours : 1; }
+int launches_per_sweep(lms_mesh_s* h, int mode) {
+    if (mode == LMS_BLOCK_GS) return std::max<int>(1, int(h->block_tc_ofs.size()) - 1);
+    return mode == LMS_COLORED_GS ? h->ncolours : 1;
+}
 
 // FP32 Jacobi and coloured GS with the direct kernel run on the work-queue sweep (rows in chunks of 4).
 bool uses_queue_sweep(const lms_mesh_s* h, int mode) {
@@ -534,6 +546,41 @@ int ensure_colours(lms_mesh_s* h) {
     LMS_TRY(lms::colour_vertices(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), h->user_perm.data(),
                                  h->colour.data(), &h->ncolours));
     h->colours_valid = true;
+    return LMS_OK;
+}
+
+// Tile of the block Gauss-Seidel: the requested one, else about three CTAs per SM and tile colour.
+int32_t block_tile_for(const lms_mesh_s* h) {
+    if (h->block_tile_req > 0) return h->block_tile_req;
+    const int64_t want = int64_t(h->n) / (int64_t(h->sms) * 24);
+    return int32_t(std::min<int64_t>(4096, std::max<int64_t>(128, want)));
+}
+
+// LMS_BLOCK_GS tables for the current ordering (lms::block_tables), uploaded.
+int ensure_block_tables(lms_mesh_s* h) {
+    const int32_t tile = block_tile_for(h);
+    if (h->block_valid && h->block_tile == tile) return LMS_OK;
+    lms::BlockTables bt;
+    LMS_TRY(lms::block_tables(h->n, h->rp.data(), h->ci.data(), h->bnd.data(), h->user_perm.data(), tile, bt));
+    if (bt.verts.empty()) bt.verts.assign(1, 0);
+    if (bt.groups.empty()) bt.groups.assign(size_t(bt.ncolours) + 1, 0);
+    if (int64_t(bt.verts.size()) > h->blk_verts_cap) {
+        LMS_TRY(h->arena.get(&h->d_blk_verts, bt.verts.size()));
+        h->blk_verts_cap = int64_t(bt.verts.size());
+    }
+    if (int64_t(bt.groups.size()) > h->blk_groups_cap) {
+        LMS_TRY(h->arena.get(&h->d_blk_groups, bt.groups.size()));
+        h->blk_groups_cap = int64_t(bt.groups.size());
+    }
+    LMS_CUDA(cudaMemcpyAsync(h->d_blk_verts, bt.verts.data(), sizeof(int32_t) * bt.verts.size(),
+                             cudaMemcpyHostToDevice, h->stream));
+    LMS_CUDA(cudaMemcpyAsync(h->d_blk_groups, bt.groups.data(), sizeof(int32_t) * bt.groups.size(),
+                             cudaMemcpyHostToDevice, h->stream));
+    LMS_CUDA(cudaStreamSynchronize(h->stream));  // the host tables die here
+    h->block_tc_ofs = bt.tc_ofs;
+    h->block_ncolours = bt.ncolours;
+    h->block_tile = tile;
+    h->block_valid = true;
     return LMS_OK;
 }
 
@@ -587,6 +634,25 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
 // base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
 int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
     const int src = (base + k1 - 1) & 1;
+    if (mode == LMS_BLOCK_GS) {  // one launch per tile colour, in place
+        lms::BlockGsArgs a{};
+        a.row_ptr = h->d_rp;
+        a.col_idx = h->d_ci;
+        a.xy = h->d_xy[base];
+        a.verts = h->d_blk_verts;
+        a.group_ofs = h->d_blk_groups;
+        a.ncolours = h->block_ncolours;
+        a.n_vertices = h->n;
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        a.recip = h->d_recip;
+        for (size_t c = 0; c + 1 < h->block_tc_ofs.size(); ++c) {
+            a.tile_begin = h->block_tc_ofs[c];
+            LMS_TRY(check_launch(lms::launch_block_gs(h->precision, a, h->block_tc_ofs[c + 1] - h->block_tc_ofs[c], s),
+                                 "block_gs"));
+        }
+        return LMS_OK;
+    }
     if (mode == LMS_INPLACE_STATIC) {
         SweepArgs a = sweep_args(h, base, base);
         a.state = stoppable ? h->d_state : nullptr;
@@ -878,6 +944,7 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     const auto t1 = std::chrono::steady_clock::now();
     h->user_perm = p;
     h->colours_valid = false;
+    h->block_valid = false;
     h->coloured_layout = false;
     LMS_TRY(apply_layout(h, p));
     LMS_TRY(build_items(h));
@@ -927,6 +994,22 @@ int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile) {
     return LMS_OK;
 }
 
+int lms_set_block_tile(lms_handle h, int32_t tile) {
+    if (!h || tile < 0) return LMS_ERR_ARG;
+    LMS_TRY(finish_stats(h));
+    if (tile != h->block_tile_req) {
+        h->block_tile_req = tile;
+        h->graphs.clear();
+    }
+    return LMS_OK;
+}
+
+int lms_get_block_tile(lms_handle h, int32_t* tile) {
+    if (!h || !tile) return LMS_ERR_ARG;
+    *tile = block_tile_for(h);
+    return LMS_OK;
+}
+
 int lms_set_fp64_arith(lms_handle h, int32_t mode) {
     if (!h || mode < LMS_FP64_ARITH_FPU || mode > LMS_FP64_ARITH_MIXED3) return LMS_ERR_ARG;
     LMS_TRY(finish_stats(h));
@@ -936,13 +1019,15 @@ int lms_set_fp64_arith(lms_handle h, int32_t mode) {
 }
 
 int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* iters_done) {
-    if (!h || max_iters < 0 || (mode != LMS_JACOBI && mode != LMS_COLORED_GS && mode != LMS_INPLACE_STATIC) ||
+    if (!h || max_iters < 0 ||
+        (mode != LMS_JACOBI && mode != LMS_COLORED_GS && mode != LMS_INPLACE_STATIC && mode != LMS_BLOCK_GS) ||
         std::isnan(tol))
         return LMS_ERR_ARG;
     if (tol >= 0.0 && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
     if (mode == LMS_COLORED_GS) LMS_TRY(ensure_coloured_layout(h));
-    if (mode == LMS_INPLACE_STATIC) LMS_TRY(ensure_ordering_layout(h));
+    if (mode == LMS_INPLACE_STATIC || mode == LMS_BLOCK_GS) LMS_TRY(ensure_ordering_layout(h));
+    if (mode == LMS_BLOCK_GS) LMS_TRY(ensure_block_tables(h));
     if (iters_done) *iters_done = 0;
     h->q_first = h->q_last = NAN;
     h->last_disp = NAN;

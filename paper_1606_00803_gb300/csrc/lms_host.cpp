@@ -516,6 +516,42 @@ int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const
     return LMS_OK;
 }
 
+int block_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                 const int32_t* new_to_old, int32_t tile, BlockTables& out) {
+    if (n <= 0 || !new_to_old || tile < 1) return LMS_ERR_ARG;
+    const int32_t ntiles = static_cast<int32_t>((static_cast<int64_t>(n) + tile - 1) / tile);
+    std::vector<int32_t> tile_colour(ntiles), order(n), colour(n);
+    int32_t ntc = 0, m = 0, nc = 0;
+    if (int rc = block_order(n, row_ptr, col_idx, is_boundary, new_to_old, tile, tile_colour.data(), &ntc,
+                             order.data(), &m))
+        return rc;
+    if (int rc = colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour.data(), &nc)) return rc;
+    nc = std::max(1, nc);
+    std::vector<int32_t> pos(n);
+    for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
+    out.verts.assign(m, 0);
+    out.groups.clear();
+    std::vector<int32_t> listed_tc;
+    int32_t cur_tile = -1;
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t v = order[i], t = pos[v] / tile;
+        if (t != cur_tile) {  // a listed tile begins: its nc + 1 group offsets start at i
+            cur_tile = t;
+            listed_tc.push_back(tile_colour[t]);
+            out.groups.resize(out.groups.size() + static_cast<size_t>(nc) + 1, i);
+        }
+        out.verts[i] = pos[v];
+        // the tile's vertices come by colour, so group c starts after every vertex of a smaller colour
+        const size_t base = out.groups.size() - static_cast<size_t>(nc) - 1;
+        for (int32_t c = colour[v] + 1; c <= nc; ++c) out.groups[base + static_cast<size_t>(c)] = i + 1;
+    }
+    out.tc_ofs.assign(static_cast<size_t>(ntc) + 1, 0);
+    for (int32_t tc : listed_tc) ++out.tc_ofs[static_cast<size_t>(tc) + 1];
+    for (int32_t c = 0; c < ntc; ++c) out.tc_ofs[static_cast<size_t>(c) + 1] += out.tc_ofs[static_cast<size_t>(c)];
+    out.ncolours = nc;
+    return LMS_OK;
+}
+
 }  // namespace lms
 
 extern "C" {
@@ -556,6 +592,31 @@ int lms_block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, c
     try {
         return lms::block_order(n, row_ptr, col_idx, is_boundary, new_to_old, tile, tile_colour, ntile_colours,
                                 order, n_order);
+    } catch (const std::bad_alloc&) {
+        return LMS_ERR_OOM;
+    }
+}
+
+int lms_block_walk(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                   const int32_t* new_to_old, int32_t tile, int32_t* seq, int32_t* nseq, int32_t* n_launches) {
+    if (!seq || !nseq || !n_launches) return LMS_ERR_ARG;
+    try {
+        lms::BlockTables bt;
+        if (int rc = lms::block_tables(n, row_ptr, col_idx, is_boundary, new_to_old, tile, bt)) return rc;
+        // the device sweep's visiting order: one launch per tile colour, block b on listed tile
+        // tc_ofs[c] + b, its colour groups in turn (order inside a group and across blocks is free)
+        int32_t m = 0, launches = 0;
+        for (size_t c = 0; c + 1 < bt.tc_ofs.size(); ++c) {
+            if (bt.tc_ofs[c + 1] > bt.tc_ofs[c]) ++launches;
+            for (int32_t t = bt.tc_ofs[c]; t < bt.tc_ofs[c + 1]; ++t) {
+                const int32_t* g = bt.groups.data() + static_cast<size_t>(t) * (bt.ncolours + 1);
+                for (int32_t k = 0; k < bt.ncolours; ++k)
+                    for (int32_t i = g[k]; i < g[k + 1]; ++i) seq[m++] = new_to_old[bt.verts[i]];
+            }
+        }
+        *nseq = m;
+        *n_launches = launches;
+        return LMS_OK;
     } catch (const std::bad_alloc&) {
         return LMS_ERR_OOM;
     }

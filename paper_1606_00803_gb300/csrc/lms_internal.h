@@ -32,6 +32,17 @@ int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const
                 const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
                 int32_t* order, int32_t* n_order);
 
+// Tables of a block Gauss-Seidel sweep (LMS_BLOCK_GS) for storage order new_to_old: verts = storage
+// positions of the interior vertices in block order; per listed tile (a tile holding interior vertices,
+// in block order) ncolours + 1 offsets of its vertex-colour groups in verts (groups[t * (ncolours + 1)
+// + c]); tiles of tile colour c are the listed tiles [tc_ofs[c], tc_ofs[c + 1]).
+struct BlockTables {
+    std::vector<int32_t> verts, groups, tc_ofs;
+    int32_t ncolours = 1;
+};
+int block_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
+                 const int32_t* new_to_old, int32_t tile, BlockTables& out);
+
 // Set the message reported with LMS_ERR_CUDA and friends (thread-local).
 void set_error_detail(const std::string& s);
 const std::string& error_detail();
@@ -72,6 +83,25 @@ struct SweepArgs {
     unsigned long long* disp2;     // max squared displacement accumulator (NULL: off)
     const double* recip;           // [kMaxRecipDeg+1] RN(1/d) for the FP64 exact division
 };
+
+// Block Gauss-Seidel sweep (k_block_gs): one CTA per tile of one tile colour; inside a tile the vertex
+// colours run one after another, separated by block barriers; positions updated in place.  Tiles of one
+// colour share no edge between interior vertices, so a launch equals the in-place sweep over its tiles
+// in block order (lms_block_order).
+struct BlockGsArgs {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    void* xy;                      // double2 / float2 positions, updated in place
+    const int32_t* verts;          // storage positions of the interior vertices in block order
+    const int32_t* group_ofs;      // [listed tile][ncolours + 1]: offsets of the tile's colour groups in verts
+    int32_t ncolours;
+    int32_t tile_begin;            // listed tile handled by block 0 of this launch
+    int32_t n_vertices;            // vertices addressable by col_idx (bounds checks of debug builds)
+    const DevState* state;         // stop flag (NULL: never stop)
+    unsigned long long* disp2;     // max squared displacement (NULL: off)
+    const double* recip;           // FP64 reciprocal table
+};
+cudaError_t launch_block_gs(int precision, const BlockGsArgs& a, int32_t n_tiles, cudaStream_t stream);
 
 // Tile-staged sweep (lms_staged.cu): items[i] = (first vertex, end vertex, first CSR entry, end entry)
 // of a tile; tiles never cross a mesh or a colour range.  row_ptr, col_idx and bnd_bits must have at

@@ -168,6 +168,72 @@ __global__ void __launch_bounds__(256, 6) k_sweep(SweepArgs a) {
     if (want) record_disp(a.disp2, d2);
 }
 
+// Block Gauss-Seidel: block b sweeps listed tile a.tile_begin + b, colour group by colour group in place,
+// with a block barrier between groups (a group's vertices are never neighbours of one another, and the
+// barrier makes the group's writes visible to the next group's reads).  FP64: Eq. 1 with sequential sums
+// (first term a copy) and the table-driven division, bit-identical to the oracle's in-place sweep in
+// block order; FP32: Kahan sums.
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_block_gs(BlockGsArgs a) {
+    if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
+    using V = typename std::conditional<FP64, double2, float2>::type;
+    __shared__ double s_recip[kMaxRecipDeg + 1];
+    if (FP64) {
+        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
+        __syncthreads();
+    }
+    V* xy = static_cast<V*>(a.xy);
+    const int32_t* g = a.group_ofs + static_cast<int64_t>(a.tile_begin + static_cast<int32_t>(blockIdx.x)) *
+                                         (a.ncolours + 1);
+    const bool want = a.disp2 != nullptr;
+    double dmax = 0.0;
+    for (int32_t c = 0; c < a.ncolours; ++c) {
+        const int32_t b = g[c], end = g[c + 1];
+        for (int32_t i = b + static_cast<int32_t>(threadIdx.x); i < end; i += static_cast<int32_t>(blockDim.x)) {
+            const int32_t v = a.verts[i];
+            const int32_t e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+            const V o = xy[v];
+            V r;
+            if constexpr (FP64) {
+                double sx = 0.0, sy = 0.0;
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int32_t u = __ldg(a.col_idx + e);
+                    if (!LMS_CHECK(u >= 0 && u < a.n_vertices)) continue;
+                    const V p = xy[u];
+                    if (e == e0) {
+                        sx = plus_zero(p.x);
+                        sy = plus_zero(p.y);
+                    } else {
+                        sx = __dadd_rn(sx, p.x);
+                        sy = __dadd_rn(sy, p.y);
+                    }
+                }
+                r.x = div_by_count(sx, e1 - e0, s_recip);
+                r.y = div_by_count(sy, e1 - e0, s_recip);
+            } else {
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int32_t u = __ldg(a.col_idx + e);
+                    if (!LMS_CHECK(u >= 0 && u < a.n_vertices)) continue;
+                    const V p = xy[u];
+                    kahan_add(sx, cx, p.x);
+                    kahan_add(sy, cy, p.y);
+                }
+                r.x = mean_f32(sx, cx, e1 - e0);
+                r.y = mean_f32(sy, cy, e1 - e0);
+            }
+            if (want) {
+                const double ex = static_cast<double>(r.x) - static_cast<double>(o.x);
+                const double ey = static_cast<double>(r.y) - static_cast<double>(o.y);
+                dmax = fmax(dmax, __fma_rn(ex, ex, __dmul_rn(ey, ey)));
+            }
+            xy[v] = r;
+        }
+        __syncthreads();
+    }
+    if (want) record_disp(a.disp2, dmax);
+}
+
 // The paper's parallel in-place sweep (Section 5.1: Algorithm 1 under a static schedule that divides the
 // vertices evenly between threads): thread t sweeps storage positions [t * per_thread, (t + 1) *
 // per_thread) in order, in place, reading each neighbour as it is at that moment - possibly already
@@ -862,6 +928,15 @@ cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int3
     k_batch_store_xy<<<n_items, 256, 0, stream>>>(items, item_mesh, new_to_old, src,
                                                   reinterpret_cast<double2*>(dst_orig), mesh_cs, bnd_bits,
                                                   reinterpret_cast<const double2*>(fixed_xy));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_gs(int precision, const BlockGsArgs& a, int32_t n_tiles, cudaStream_t stream) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (precision == LMS_FP64)
+        k_block_gs<true><<<n_tiles, 256, 0, stream>>>(a);
+    else
+        k_block_gs<false><<<n_tiles, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

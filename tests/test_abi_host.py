@@ -241,3 +241,16 @@ def test_block_order_rejects_bad_arguments():
                                     p.ctypes.data, 8, out.ctypes.data, ctypes.byref(nt), out.ctypes.data,
                                     ctypes.byref(k))
     assert rc == -1
+
+
+@pytest.mark.parametrize("ordering", [oracle.ORI, oracle.BFS, oracle.RDR, oracle.RANDOM])
+def test_block_gs_tables_walk_in_oracle_order(ordering):
+    # the device sweep's tables walked in launch order visit the oracle's block order
+    for m in (meshgen.workload(1, side=37), meshgen.workload(2, side=23), meshgen.workload(0)):
+        p = oracle.order(m, ordering, seed=4)
+        colour, nc = oracle.color_greedy(m["row_ptr"], m["col_idx"], m["is_boundary"], p)
+        for tile in (1, 7, 128, 333, m["n"] + 2):
+            want, _, nt = oracle.block_sequence(m["row_ptr"], m["col_idx"], m["is_boundary"], p, colour, nc, tile)
+            got, launches = lms.block_walk(m["row_ptr"], m["col_idx"], m["is_boundary"], p, tile)
+            assert np.array_equal(got, want)
+            assert 1 <= launches <= nt
