@@ -253,7 +253,7 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
 int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
 
 /* Tile of LMS_BLOCK_GS sweeps in storage positions (tile >= 1), or 0 to choose it by mesh size (about
-   three CTAs per SM for each tile colour, within 128..4096).  The sweep's result depends on the tile
+   eight tiles per SM, within 128..1024).  The sweep's result depends on the tile
    (it fixes the order).  lms_get_block_tile returns the tile the next sweep uses.  [host] */
 int lms_set_block_tile(lms_handle h, int32_t tile);
 int lms_get_block_tile(lms_handle h, int32_t* tile);

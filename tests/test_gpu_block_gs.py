@@ -56,7 +56,7 @@ def test_block_gs_mixed_with_other_modes_and_automatic_tile():
     with lms.Mesh.from_dict(m, lms.FP64) as g:
         g.reorder(lms.BFS)
         tile = g.block_tile()  # chosen by mesh size
-        assert 128 <= tile <= 4096
+        assert 128 <= tile <= 1024
         g.smooth(3, mode=lms.COLORED_GS)  # colour-major layout, then back to the ordering's
         g.smooth(4, mode=lms.BLOCK_GS)
         g.smooth(2)
