@@ -583,6 +583,7 @@ int ensure_block_tables(lms_mesh_s* h) {
     h->block_ncolours = bt.ncolours;
     h->block_tile = tile;
     h->block_valid = true;
+    h->graphs.clear();  // captured sweeps hold the old tables' pointers and launch counts
     return LMS_OK;
 }
 
