@@ -254,3 +254,21 @@ def test_block_gs_tables_walk_in_oracle_order(ordering):
             got, launches = lms.block_walk(m["row_ptr"], m["col_idx"], m["is_boundary"], p, tile)
             assert np.array_equal(got, want)
             assert 1 <= launches <= nt
+
+
+def test_handle_setters_reject_null_and_bad_values_without_device_work():
+    L = lms._lib()
+    t = ctypes.c_int32()
+    assert L.lms_set_fp64_arith(None, 0) == -1
+    assert L.lms_set_block_tile(None, 64) == -1
+    assert L.lms_get_block_tile(None, ctypes.byref(t)) == -1
+    assert L.lms_set_inplace_split(None, 1) == -1
+    assert L.lms_set_launch(None, 0, 128, 512) == -1
+    assert L.lms_smooth(None, 1, 0, -1.0, None) == -1
+    # the integer-pipe self-tests check their arguments before any device work
+    assert L.lms_selftest_add64(-1, None, None, None) == -1
+    assert L.lms_selftest_divint64(-1, None, None, None) == -1
+    d = np.array([0], np.int32)
+    s = np.zeros(1)
+    assert L.lms_selftest_divint64(1, s.ctypes.data, d.ctypes.data, s.ctypes.data) == -1  # divisor 0
+    assert L.lms_selftest_add64(0, None, None, None) == 0  # nothing to do
