@@ -272,3 +272,34 @@ def test_handle_setters_reject_null_and_bad_values_without_device_work():
     s = np.zeros(1)
     assert L.lms_selftest_divint64(1, s.ctypes.data, d.ctypes.data, s.ctypes.data) == -1  # divisor 0
     assert L.lms_selftest_add64(0, None, None, None) == 0  # nothing to do
+
+
+def test_plain_c_program_uses_the_library(tmp_path):
+    # the header is plain C99 and a C program can link liblms.so and call its host entry points
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "lms.h"
+int main(void) {
+    /* path 0-1-2-3 with fixed ends: validate, order, colour */
+    int32_t rp[5] = {0, 1, 3, 5, 6}, ci[6] = {1, 0, 2, 1, 3, 2}, perm[4], colour[4], nc = 0;
+    uint8_t bnd[4] = {1, 0, 0, 1};
+    if (lms_validate(4, rp, ci, bnd, 0, NULL) != LMS_OK) return 1;
+    if (lms_order_host(4, rp, ci, bnd, NULL, LMS_BFS, 0, perm) != LMS_OK) return 2;
+    if (lms_color_host(4, rp, ci, bnd, perm, colour, &nc) != LMS_OK || nc != 2) return 3;
+    if (strlen(lms_error_string(LMS_ERR_CSR)) == 0) return 4;
+    printf("%d %d %d %d\n", perm[0], perm[1], perm[2], perm[3]);
+    return 0;
+}
+""")
+    lib = lms.library_path()
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    out = subprocess.run([str(exe)], stdout=subprocess.PIPE, check=True).stdout.decode().split()
+    assert out == ["0", "1", "2", "3"]
