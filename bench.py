@@ -14,8 +14,9 @@ dominant kernel, the oracle timed on host cores, clocks under load.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--full]
 
-Under torchrun (N > 1) every rank smooths its own 512-mesh batch (weak
-scaling, no collective on the data path); timings are max-reduced over ranks.
+Under torchrun (N > 1) the 512-mesh batch is split between the ranks by whole
+meshes, balanced by vertex count (strong scaling; meshes share nothing, so no
+collective on the data path); timings are max-reduced over ranks.
 """
 import argparse
 import json
@@ -107,19 +108,26 @@ class Dist:
             self.pg.destroy_process_group()
 
 
-def rank_mesh_seeds(count, rank):
-    """Seeds of the meshes rank `rank` smooths: rank 0 has the 512-mesh workload itself; other ranks
-    get as many different meshes of the same size distribution (weak scaling)."""
+def batch_meshes(count, lo=32, hi=448):
+    """The headline's batch: `count` meshes built as the 1024 x 1024 workload (10% flips, 5% centroid
+    splits) with sides log-uniform in [lo, hi]."""
     import meshgen
+    sides = meshgen.batch_sides(count, lo, hi)
     base = meshgen.BASE_SEED + 3 + 1000
-    return [base + rank * count + m for m in range(count)]
+    return [meshgen.generate(s, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=base + m)
+            for m, s in enumerate(sides)]
 
 
-def batch_for_rank(count, rank):
-    import meshgen
-    sides = meshgen.batch_sides(count)
-    seeds = rank_mesh_seeds(count, rank)
-    return [meshgen.generate(s, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=sd) for s, sd in zip(sides, seeds)]
+def rank_batch(count, rank, world, lo=32, hi=448):
+    """This rank's share of one batch: whole meshes balanced by vertex count between the `world` ranks
+    (lms_partition_meshes).  Returns (meshes, their indices in the batch, vertices per rank)."""
+    import paper_1606_00803_gb300 as lms
+    meshes = batch_meshes(count, lo, hi)
+    if world == 1:
+        return meshes, list(range(len(meshes))), [sum(m["n"] for m in meshes)]
+    rank_of, load = lms.partition_meshes([m["n"] for m in meshes], world)
+    mine = [i for i in range(len(meshes)) if rank_of[i] == rank]
+    return [meshes[i] for i in mine], mine, [int(x) for x in load]
 
 
 # ------------------------------------------------------------------ helpers
@@ -224,6 +232,57 @@ def cpu_rate_oracle(meshes, sweeps, budget_s):
     return updates / spent, dict(meshes=used, vertices=verts, sweeps=sweeps, seconds=spent)
 
 
+def diag_of(m):
+    import numpy as np
+    return math.hypot(float(np.ptp(m["xy"][:, 0])), float(np.ptp(m["xy"][:, 1])))
+
+
+def err_over_diag(got, want, m):
+    import numpy as np
+    return float(np.abs(np.asarray(got) - np.asarray(want)).max() / diag_of(m))
+
+
+def batch_err(all_xy, meshes, wants):
+    """Largest max |x_gpu - x_oracle| / bbox diagonal over the meshes of a batch."""
+    worst, o = 0.0, 0
+    for m, w in zip(meshes, wants):
+        worst = max(worst, err_over_diag(all_xy[o:o + m["n"]], w, m))
+        o += m["n"]
+    return worst
+
+
+def cpu_baseline_batch(meshes, sweeps, repeats=3):
+    """The oracle's Jacobi (one thread, as it stands) over the whole batch, `repeats` times: median rate and
+    the outputs of the first run (the FP64 results the GPU's FP32 results are compared with).  Beside it,
+    the same sweeps with the vertex loop under an OpenMP static schedule on every host core (the paper's
+    Section 5.1 setup; a separate timing copy of the oracle's arithmetic, bit-identical to it)."""
+    import oracle
+    n_int = sum(int((m["is_boundary"] == 0).sum()) for m in meshes)
+    outs, times = None, []
+    for r in range(repeats):
+        t = time.perf_counter()
+        res = [oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps)[0] for m in meshes]
+        times.append(time.perf_counter() - t)
+        if outs is None:
+            outs = res
+    rate = n_int * sweeps / statistics.median(times)
+    omp = None
+    try:
+        omp_times, used = [], 0
+        for r in range(repeats):
+            t = time.perf_counter()
+            for m in meshes:
+                _, used = oracle.jacobi_omp(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps, 0)
+            omp_times.append(time.perf_counter() - t)
+        omp = {"value": n_int * sweeps / statistics.median(omp_times), "unit": UNIT, "cores": used,
+               "nproc": os.cpu_count(), "seconds": [round(x, 2) for x in omp_times],
+               "kind": "the oracle's Jacobi arithmetic with the vertex loop under omp parallel for "
+                       "schedule(static) on every host core (timing context, bit-identical results)"}
+    except Exception as e:  # noqa: BLE001
+        omp = {"unavailable": "OpenMP baseline not built: %s" % e}
+    return rate, [round(x, 2) for x in times], outs, omp
+
+
 def cpu_orderings_oracle():
     """The paper's serial experiment on the host: the 1024 x 1024 mesh stored under each ordering (CSR rows
     and positions relabelled by the oracle), then one oracle in-place sweep in storage order (Algorithm 1,
@@ -284,26 +343,38 @@ def reuse_row(lms, m, new_to_old, both):
 
 
 def per_ordering_table(hbm_peak):
-    """1024 x 1024 workload: every ordering x {FP64, FP32} x {Jacobi, coloured GS}, 100 sweeps."""
+    """1024 x 1024 workload: every ordering x {FP64, FP32} x {Jacobi, coloured GS, in-place static}, 100
+    sweeps, each result compared with the FP64 oracle after the same sweeps from the same start: Jacobi
+    with the oracle's Jacobi (the same for every ordering), coloured GS with the oracle's in-place sweep in
+    (colour, storage position) order of that ordering; the in-place static form (racy, timing-dependent)
+    with the oracle's sequential in-place sweep in storage order, reported without a bound."""
+    import numpy as np
     import torch
     import meshgen
+    import oracle
     import paper_1606_00803_gb300 as lms
     m = meshgen.workload(1)
     n, nnz = m["n"], m["nnz"]
     n_int = int((m["is_boundary"] == 0).sum())
-    deg = m["row_ptr"][1:] - m["row_ptr"][:-1]
-    nnz_int = int(deg[m["is_boundary"] == 0].sum())
     stream = torch.cuda.current_stream()
+    want_jacobi, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], PER_ORDERING_SWEEPS)
     rows = {}
     for oname, o in ORDERINGS:
+        want = {}
         for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
             g = lms.Mesh.from_dict(m, p)
             t0 = time.perf_counter()
             g.reorder(o, seed=meshgen.BASE_SEED + 7)
             reorder_ms = (time.perf_counter() - t0) * 1e3
             order_ms, layout_ms = g.last_reorder_ms()
+            perm = g.permutation()
+            if not want:
+                want["jacobi"] = want_jacobi
+                want["gs"], _, _ = oracle.gs_smooth(m, perm, PER_ORDERING_SWEEPS)
+                want["inplace_static"], _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"],
+                                                             PER_ORDERING_SWEEPS, mode=oracle.INPLACE, seq=perm)
             if p == lms.FP64:
-                rows["%s/reuse" % oname] = reuse_row(lms, m, g.permutation(), both=True)
+                rows["%s/reuse" % oname] = reuse_row(lms, m, perm, both=True)
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS), ("inplace_static", lms.INPLACE_STATIC)):
                 g.smooth(PER_ORDERING_SWEEPS, mode=mode)  # warm-up + graph capture
                 torch.cuda.synchronize()
@@ -315,9 +386,13 @@ def per_ordering_table(hbm_peak):
                            algorithmic_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 3))
                 if mode == lms.COLORED_GS:
                     row["colours"] = g.colors()[1]
-                if p == lms.FP64:
-                    ops = fp64_ops(n_int, nnz_int) / (sweep_ms * 1e-3)
-                    row["fp64_ops_per_s"] = ops
+                g.set_coords(m["xy"])
+                g.smooth(PER_ORDERING_SWEEPS, mode=mode)
+                e = err_over_diag(g.coords(), want[mname], m)
+                if mode == lms.INPLACE_STATIC:
+                    row["diff_vs_sequential_inplace_over_diag"] = e  # a race: no bound applies
+                else:
+                    row["err_vs_oracle_over_diag"] = e
                 rows["%s/%s/%s" % (oname, pname, mname)] = row
             rows["%s/%s/reorder_ms" % (oname, pname)] = dict(total=round(reorder_ms, 2), ordering=round(order_ms, 2),
                                                              layout=round(layout_ms, 2))
@@ -330,46 +405,118 @@ def per_ordering_table(hbm_peak):
                 ms = min(time_graph(lambda: g.smooth(PER_ORDERING_SWEEPS), stream, 1) for _ in range(3))
                 sweep_ms = ms / PER_ORDERING_SWEEPS
                 ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
+                g.set_coords(m["xy"])
+                g.smooth(PER_ORDERING_SWEEPS)
                 rows["%s/%s/jacobi_staged" % (oname, pname)] = dict(
                     updates_per_s=n_int / (sweep_ms * 1e-3), sweep_ms=round(sweep_ms, 5),
-                    algorithmic_gbs=round(ab / (sweep_ms * 1e-3) / 1e9, 1))
+                    algorithmic_gbs=round(ab / (sweep_ms * 1e-3) / 1e9, 1),
+                    err_vs_oracle_over_diag=err_over_diag(g.coords(), want_jacobi, m))
             g.close()
     return dict(workload="1024x1024 jittered grid + 10%% flips + 5%% splits (%d vertices, %d interior, %d CSR "
-                         "entries), %d sweeps; working set fits in L2 at FP32, so GB/s may exceed HBM" %
+                         "entries), %d sweeps; working set fits in L2 at FP32, so GB/s may exceed HBM; "
+                         "err_vs_oracle_over_diag = max |x - x_oracle| / bbox diagonal after the same sweeps" %
                          (n, n_int, nnz, PER_ORDERING_SWEEPS), rows=rows)
 
 
-def stopping_table():
+STOP_TOL, STOP_CAP = 5e-6, 200
+
+
+def oracle_stop_sweeps(task):
+    """Where the FP64 oracle's Section 5.1 rule fires on the graded 2048 x 2048 mesh: task = (ordering name,
+    ordering id, mode name).  Runs in a spawned worker process (the per-sweep quality makes these runs the
+    bulk of the benchmark's oracle time, and they are independent)."""
+    import meshgen
+    import oracle
+    oname, o, mname = task
+    m = meshgen.workload(2)
+    if mname == "jacobi":
+        _, k, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], STOP_CAP, tri=m["tri"],
+                                tol=STOP_TOL)
+    else:
+        _, k, _ = oracle.gs_smooth(m, oracle.order(m, o, seed=meshgen.BASE_SEED + 7), STOP_CAP, tol=STOP_TOL)
+    return "%s/%s" % (oname, mname), k
+
+
+def start_oracle_stop_sweeps():
+    """Start the oracle's stop-sweep runs in a spawn-context process pool (never forked after CUDA
+    initialisation); returns (pool, async result) or None when no pool can be started."""
+    import multiprocessing as mp
+    tasks = [("all", 0, "jacobi")] + [(o, i, "gs") for o, i in ORDERINGS if o != "random"]
+    try:
+        pool = mp.get_context("spawn").Pool(min(len(tasks), max(1, (os.cpu_count() or 2) - 2)))
+        return pool, pool.map_async(oracle_stop_sweeps, tasks)
+    except Exception as e:  # noqa: BLE001
+        log("oracle stop-sweep pool not started: %s" % e)
+        return None
+
+
+def finish_oracle_stop_sweeps(handle):
+    if handle is None:
+        return {}
+    pool, res = handle
+    try:
+        return dict(res.get(timeout=900))
+    except Exception as e:  # noqa: BLE001
+        log("oracle stop-sweep runs failed: %s" % e)
+        return {}
+    finally:
+        pool.close()
+        pool.join()
+
+
+def stopping_table(oracle_sweeps):
     """Graded 2048 x 2048 workload, FP32: sweeps until the Section 5.1 rule fires (quality gain < 5e-6, cap
     200) for each ordering and sweep mode, with the device time and the qualities before and after.  The
-    paper reports that the ordering does not change the count (exactly true for Jacobi here)."""
+    paper reports that the ordering does not change the count (exactly true for Jacobi here).  Each result
+    is compared with the FP64 oracle run for the GPU's sweep count (Jacobi: the oracle's Jacobi; coloured
+    GS: the oracle's in-place sweep in that ordering's colour order); beside it, the sweep at which the
+    FP64 oracle's own rule fires (for Jacobi, the same under every ordering)."""
     import meshgen
+    import oracle
     import paper_1606_00803_gb300 as lms
     m = meshgen.workload(2)
+    tol, cap = STOP_TOL, STOP_CAP
+    jacobi_at = {}
     rows = {}
     for oname, o in ORDERINGS:
         if oname == "random":
             continue
         with lms.Mesh.from_dict(m, lms.FP32) as g:
             g.reorder(o, seed=meshgen.BASE_SEED + 7)
+            perm = g.permutation()
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS), ("inplace_static", lms.INPLACE_STATIC)):
                 g.set_coords(m["xy"])
-                k = g.smooth(200, mode=mode, tol=5e-6)
+                k = g.smooth(cap, mode=mode, tol=tol)
                 st = g.last_stats()
-                rows["%s/%s" % (oname, mname)] = dict(sweeps=k, ms=round(st["ms"], 3), q_first=st["q_first"],
-                                                      q_last=st["q_last"])
+                row = dict(sweeps=k, ms=round(st["ms"], 3), q_first=st["q_first"], q_last=st["q_last"])
+                got = g.coords()
+                if mode == lms.JACOBI:
+                    if k not in jacobi_at:
+                        jacobi_at[k], _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], k)
+                    row["err_vs_oracle_over_diag"] = err_over_diag(got, jacobi_at[k], m)
+                    row["oracle_sweeps"] = oracle_sweeps.get("all/jacobi")
+                elif mode == lms.COLORED_GS:
+                    want, _, _ = oracle.gs_smooth(m, perm, k)
+                    row["err_vs_oracle_over_diag"] = err_over_diag(got, want, m)
+                    row["oracle_sweeps"] = oracle_sweeps.get("%s/gs" % oname)
+                rows["%s/%s" % (oname, mname)] = row
     return dict(workload="2048 x 2048 graded mesh (%d vertices), FP32, stop when the mean quality gains less than "
                          "5e-6 in a sweep (cap 200); in-place static = the paper's parallel form, one GPU thread per "
-                         "resident slot" % m["n"], rows=rows)
+                         "resident slot (a race: no oracle result to compare with); err_vs_oracle_over_diag = max "
+                         "|x - x_oracle| / bbox diagonal with the oracle run for the GPU's sweep count; oracle_sweeps "
+                         "= where the FP64 oracle's rule fires" % m["n"], rows=rows)
 
 
-def batched_per_ordering(meshes, cfg, hbm_peak, ab):
+def batched_per_ordering(meshes, cfg, hbm_peak, ab, wants):
     """The 512-mesh batch stored under every ordering, the headline's launch configuration, 50-sweep steps
-    (best of 3 timings of 5 steps)."""
+    (best of 3 timings of 5 steps); each ordering's result after one 50-sweep step from the meshes' initial
+    coordinates compared with the FP64 oracle's Jacobi (`wants`, the same for every ordering)."""
+    import numpy as np
     import torch
     import paper_1606_00803_gb300 as lms
     rows = {}
     stream = torch.cuda.current_stream()
+    xy0 = np.concatenate([m["xy"] for m in meshes])
     for oname, o in ORDERINGS:
         t0 = time.perf_counter()
         with lms.Batch(meshes, ordering=o, seed=7) as b:
@@ -381,24 +528,75 @@ def batched_per_ordering(meshes, cfg, hbm_peak, ab):
             ms = min(time_graph(lambda: b.smooth(SWEEPS_PER_STEP), stream, 5) for _ in range(3))
             sweep_ms = ms / SWEEPS_PER_STEP
             gbs = ab / (sweep_ms * 1e-3) / 1e9
+            b.set_all_coords(xy0)
+            b.smooth(SWEEPS_PER_STEP)
             rows[oname] = dict(updates_per_s=n_int / (sweep_ms * 1e-3), sweep_ms=round(sweep_ms, 5),
                                algorithmic_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 3),
-                               create_s=round(create_s, 2))
-    return dict(workload="the headline's 512-mesh batch under each ordering, FP32 Jacobi, launch %s" % cfg, rows=rows)
+                               create_s=round(create_s, 2),
+                               err_vs_oracle_over_diag=batch_err(b.all_coords(), meshes, wants))
+    return dict(workload="the headline's 512-mesh batch under each ordering, FP32 Jacobi, launch %s; "
+                         "err_vs_oracle_over_diag = the largest max |x - x_oracle| / bbox diagonal over the meshes "
+                         "after %d sweeps" % (cfg, SWEEPS_PER_STEP), rows=rows)
+
+
+def fp64_plain_table(hbm_peak):
+    """FP64 plain form beside the FP32 batched headline: the 4096 x 4096 mesh (~18.4M vertices, positions
+    larger than L2) in the RDR ordering, Jacobi, 20-sweep graphs, FP64 and FP32; each result after 20 sweeps
+    compared with the FP64 oracle."""
+    import torch
+    import meshgen
+    import oracle
+    import paper_1606_00803_gb300 as lms
+    sweeps = 20
+    m = meshgen.workload(4)
+    n, nnz = m["n"], m["nnz"]
+    n_int = int((m["is_boundary"] == 0).sum())
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
+        with lms.Mesh.from_dict(m, p) as g:
+            t0 = time.perf_counter()
+            g.reorder(lms.RDR)
+            reorder_s = time.perf_counter() - t0
+            g.smooth(sweeps)
+            torch.cuda.synchronize()
+            ms = min(time_graph(lambda: g.smooth(sweeps), stream, 1) for _ in range(3)) / sweeps
+            ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
+            gbs = ab / (ms * 1e-3) / 1e9
+            g.set_coords(m["xy"])
+            g.smooth(sweeps)
+            rows[pname] = dict(updates_per_s=n_int / (ms * 1e-3), sweep_ms=round(ms, 4),
+                               algorithmic_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 3),
+                               roofline={"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                         "frac": gbs / hbm_peak},
+                               err_vs_oracle_over_diag=err_over_diag(g.coords(), want, m),
+                               reorder_s=round(reorder_s, 2))
+    rows["fp64"]["arithmetic"] = ("IEEE FP64, bit-identical to the oracle; divisions and every third add of a row on "
+                                  "32-bit integer instructions, the other adds on the FP64 unit "
+                                  "(LMS_FP64_ARITH_MIXED3); the FP64 unit and integer issue, not HBM, bound it")
+    return dict(workload="4096 x 4096 jittered grid + 10%% flips + 5%% splits (%d vertices, %d interior), RDR, "
+                         "Jacobi, %d-sweep graphs; algorithmic bytes per sweep FP64 %.0f MB, FP32 %.0f MB" %
+                         (n, n_int, sweeps, algorithmic_bytes_fp64(n, n_int, nnz) / 1e6,
+                          algorithmic_bytes_fp32(n, n_int, nnz) / 1e6), rows=rows)
 
 
 def large_table(hbm_peak):
     """4096 x 4096 workload (~18.4M vertices, positions larger than L2): every ordering, FP64 vs FP32,
-    Jacobi and coloured GS."""
+    Jacobi and coloured GS, each result after 20 sweeps compared with the FP64 oracle (Jacobi: the oracle's
+    Jacobi; coloured GS: the oracle's in-place sweep in that ordering's colour order)."""
     import torch
     import meshgen
+    import oracle
     import paper_1606_00803_gb300 as lms
     m = meshgen.workload(4)
     n, nnz = m["n"], m["nnz"]
     n_int = int((m["is_boundary"] == 0).sum())
     stream = torch.cuda.current_stream()
+    want_jacobi, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 20)
     rows = {}
     for oname, o in ORDERINGS:
+        want_gs = None
         for pname, p in (("fp64", lms.FP64), ("fp32", lms.FP32)):
             g = lms.Mesh.from_dict(m, p)
             t0 = time.perf_counter()
@@ -408,15 +606,20 @@ def large_table(hbm_peak):
                 total=round((time.perf_counter() - t0) * 1e3, 1), ordering=round(order_ms, 1), layout=round(layout_ms, 1))
             if p == lms.FP64:
                 rows["%s/reuse" % oname] = reuse_row(lms, m, g.permutation(), both=False)
+            if want_gs is None:
+                want_gs, _, _ = oracle.gs_smooth(m, g.permutation(), 20)
             for mname, mode in (("jacobi", lms.JACOBI), ("gs", lms.COLORED_GS)):
                 g.smooth(20, mode=mode)
                 torch.cuda.synchronize()
                 ms = min(time_graph(lambda: g.smooth(20, mode=mode), stream, 1) for _ in range(3)) / 20
                 ab = (algorithmic_bytes_fp64 if p == lms.FP64 else algorithmic_bytes_fp32)(n, n_int, nnz)
                 gbs = ab / (ms * 1e-3) / 1e9
+                g.set_coords(m["xy"])
+                g.smooth(20, mode=mode)
                 rows["%s/%s/%s" % (oname, pname, mname)] = dict(
                     updates_per_s=n_int / (ms * 1e-3), sweep_ms=round(ms, 4), algorithmic_gbs=round(gbs, 1),
-                    hbm_frac=round(gbs / hbm_peak, 3))
+                    hbm_frac=round(gbs / hbm_peak, 3),
+                    err_vs_oracle_over_diag=err_over_diag(g.coords(), want_jacobi if mode == lms.JACOBI else want_gs, m))
             g.close()
     rows["gs_to_tol"] = gs_to_tol(m)
     return dict(workload="4096x4096 jittered grid + flips/splits (%d vertices), 20-sweep graphs" % n, rows=rows)
@@ -462,9 +665,12 @@ def run_ours(args, dist):
     import torch
     import paper_1606_00803_gb300 as lms
 
+    extras_wanted = dist.rank == 0 and not args.skip_extras
+    # the oracle's stop-sweep runs go to a spawned pool before any GPU work and are collected later
+    stop_pool = start_oracle_stop_sweeps() if extras_wanted and dist.world == 1 else None
     torch.cuda.set_device(dist.local if dist.world > 1 else 0)
     hbm_peak, peak_kind = measured_peaks()
-    meshes = batch_for_rank(args.meshes, dist.rank)
+    meshes, mine, rank_load = rank_batch(args.meshes, dist.rank, dist.world)
     t0 = time.perf_counter()
     b = lms.Batch(meshes, ordering=lms.RDR)
     create_s = time.perf_counter() - t0
@@ -508,7 +714,8 @@ def run_ours(args, dist):
 
     # end to end through the public API: page-locked host coordinates in, 50 sweeps, coordinates out, one
     # lms_batch_run call per step (copies of one group of meshes overlap the sweeps of the others)
-    xy_in = torch.from_numpy(np.concatenate([m["xy"] for m in meshes])).pin_memory()
+    xy0 = np.concatenate([m["xy"] for m in meshes])
+    xy_in = torch.from_numpy(xy0).pin_memory()
     xy_out = torch.empty_like(xy_in).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
 
@@ -528,45 +735,50 @@ def run_ours(args, dist):
         % (value, ms_step, sweep_ms, achieved, achieved / hbm_peak, e2e_value))
     h2d = int(xy_in.numel() * 8)
     d2h = int(xy_out.numel() * 8)
+    # the headline's result: one 50-sweep step from the meshes' initial coordinates
+    b.set_all_coords(xy0)
+    b.smooth(SWEEPS_PER_STEP)
+    gpu_xy = b.all_coords()
 
     extras = {}
-    if dist.rank == 0 and not args.skip_extras:
+    if extras_wanted:
         extras["per_ordering"] = per_ordering_table(hbm_peak)
-        rdr = extras["per_ordering"]["rows"]["rdr/fp64/jacobi"]
-        extras["fp64_plain"] = dict(
-            workload="1024x1024, RDR, Jacobi, 100 sweeps", updates_per_s=rdr["updates_per_s"],
-            arithmetic="IEEE FP64, bit-identical to the oracle; divisions and every third add of a row on 32-bit "
-                       "integer instructions, the other adds on the FP64 unit (LMS_FP64_ARITH_MIXED3)",
-            roofline=dict(bound="alu", achieved=rdr["fp64_ops_per_s"] / 1e9, peak=2 * 152 * 2.07,
-                          unit="G IEEE FP64 ops/s", frac=round(rdr["fp64_ops_per_s"] / 1e9 / (2 * 152 * 2.07), 3),
-                          peak_note=FP64_OPS_PEAK_NOTE),
-            hbm_frac=rdr["hbm_frac"])
-        extras["stopping_rule"] = stopping_table()
-        extras["batched_per_ordering"] = batched_per_ordering(meshes, cfg, hbm_peak, ab)
+        extras["fp64_plain"] = fp64_plain_table(hbm_peak)
+        extras["stopping_rule"] = stopping_table(finish_oracle_stop_sweeps(stop_pool))
         if args.full:
             extras["large"] = large_table(hbm_peak)
-    cpu = None
+    cpu, err = None, None
     if dist.rank == 0 and dist.world == 1:
-        rate, sample = cpu_rate_oracle(meshes, SWEEPS_PER_STEP, 10.0)
+        rate, times, wants, omp = cpu_baseline_batch(meshes, SWEEPS_PER_STEP)
+        err = batch_err(gpu_xy, meshes, wants)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d of the %d meshes (%d vertices), %d Jacobi sweeps each, FP64, one thread, %.1f s"
-                         % (sample["meshes"], k, sample["vertices"], sample["sweeps"], sample["seconds"])}
+               "sample": "all %d meshes (%d vertices), %d Jacobi sweeps each, FP64 oracle as it stands, one thread; "
+                         "median of 3 runs (%s s)" % (k, n, SWEEPS_PER_STEP, ", ".join(str(t) for t in times)),
+               "all_cores": omp}
         if not args.skip_extras:
             cpu["per_ordering"] = cpu_orderings_oracle()
+            extras["batched_per_ordering"] = batched_per_ordering(meshes, cfg, hbm_peak, ab, wants)
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {
                 "workload": "batched FP32 Jacobi: %d meshes (jittered grid, 10%% flips, 5%% centroid splits, side "
                             "log-uniform 32..448), RDR ordering, %d sweeps per step replayed from one CUDA graph"
-                            % (k, SWEEPS_PER_STEP),
-                "meshes": k, "vertices": n, "interior_vertices": n_int, "csr_entries": nnz,
+                            % (args.meshes, SWEEPS_PER_STEP),
+                "meshes": args.meshes, "vertices": n, "interior_vertices": n_int, "csr_entries": nnz,
                 "sweeps_per_step": SWEEPS_PER_STEP, "ordering": "rdr", "precision": "fp32 (Kahan sums)",
                 "l2": "inputs larger than L2: %.2f GB moved per sweep vs 129 MB L2" % (ab / 1e9),
-                "launch": cfg, "parallelism": "each rank smooths its own batch" if dist.world > 1 else "1 GPU",
+                "launch": cfg,
+                "parallelism": ("1 GPU" if dist.world == 1 else
+                                "the batch split by whole meshes, balanced by vertex count (vertices per rank %s); "
+                                "rank 0's counts shown" % rank_load),
                 "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2)},
+            "err_vs_oracle_over_diag": err,
+            "err_note": ("largest max |x_gpu - x_oracle| / bbox diagonal over the %d meshes after one %d-sweep step "
+                         "from their initial coordinates (FP32 with Kahan sums vs the FP64 oracle; bound 2e-6)"
+                         % (k, SWEEPS_PER_STEP)) if err is not None else "computed at N = 1 only",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None, "kernel": {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"]}.get(
                              cfg["kernel"], "k_batch_sweep<%d>" % cfg["chunk"]),
@@ -647,7 +859,7 @@ def run_reference(args, dist):
     """The oracle as it stands, on the host cores, over a bounded sample of the same workload."""
     if dist.rank != 0:
         return
-    meshes = batch_for_rank(args.meshes, 0)
+    meshes = batch_meshes(args.meshes)
     import oracle
     # size the per-step sample so that (warmup + steps) steps take about a minute
     per_step_s = max(0.05, 60.0 / (args.steps + max(3, args.warmup)))

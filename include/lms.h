@@ -208,6 +208,18 @@ int lms_block_walk(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
                    const int32_t* new_to_old, int32_t tile, int32_t* seq, int32_t* nseq, int32_t* n_launches);
 
 /*
+ * Split a batch of k independent meshes between `ranks` GPUs by whole meshes, balanced by vertex count
+ * (the paper splits one mesh's vertices evenly between threads, Section 5.1; meshes of a batch share no
+ * vertex, so whole meshes need no exchange between GPUs).  Longest-processing-time rule: meshes taken by
+ * vertex count, largest first (ties by index), each to the rank with the smallest load so far (ties to
+ * the lowest rank).  Every mesh lands on exactly one rank and the most loaded rank exceeds the least
+ * loaded by at most the largest mesh.  n_vertices: [k] counts (>= 1); rank_of: [k] output; load: [ranks]
+ * output of vertices per rank (may be NULL).  Deterministic.  LMS_ERR_ARG (NULL, k < 1, ranks < 1, a count
+ * < 1).  [host]
+ */
+int lms_partition_meshes(int32_t k, const int32_t* n_vertices, int32_t ranks, int32_t* rank_of, int64_t* load);
+
+/*
  * Create a smoothing handle: validates the mesh (as lms_validate), copies it
  * to the device and stores the coordinates in `precision`.  The initial
  * ordering is LMS_ORI.  tri may be NULL (ntri = 0); quality, LMS_RDR and the
@@ -294,6 +306,11 @@ int lms_get_csr(lms_handle h, int32_t* row_ptr, int32_t* col_idx, int32_t* stora
    device time in ms, Q before and after (NaN when no stopping rule ran).  Any pointer may be NULL. */
 int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, double* q_last);
 
+/* The displacement check and device time of the last lms_smooth alone: the same as lms_last_stats with
+   q_first and q_last left out (max_disp = largest vertex displacement of the final sweep in original
+   units, ms = device time).  Any pointer may be NULL. */
+int lms_last_error_stats(lms_handle h, double* max_disp, double* ms);
+
 /* Number of GPU threads (contiguous blocks of the storage order) of LMS_INPLACE_STATIC sweeps; 0 = one
    per resident thread slot of the device (the default), 1 = the sequential Algorithm 1.  [host] */
 int lms_set_inplace_split(lms_handle h, int32_t threads);
@@ -312,14 +329,17 @@ void lms_destroy(lms_handle h);
  * under a fixed device-memory budget, services that forbid allocations on their steady-state path).
  * All buffers are the caller's DEVICE pointers: row_ptr [n+1] and col_idx [row_ptr[n]] (CSR, as for
  * lms_create), is_boundary [n] (nonzero = fixed), xy [2n] interleaved positions (input; receives the
- * result), xy_tmp [2n] work buffer (needs no initial contents; distinct from xy).  Runs `iters` sweeps of
- * Eq. 1 on cuda_stream (NULL = legacy default stream), asynchronously; results equal lms_smooth's FP64
- * Jacobi bit for bit (sequential row-order sums, IEEE division).  The mesh is not validated.
+ * result), xy_tmp [2n] work buffer (needs no initial contents; must not overlap xy, else LMS_ERR_ARG).
+ * Runs `iters` sweeps on cuda_stream (NULL = legacy default stream), asynchronously: in each sweep every
+ * interior vertex moves to the mean of its neighbours' positions and boundary vertices stay put.  Results
+ * equal lms_smooth's FP64 Jacobi bit for bit (sums in stored row order, one IEEE division).  The mesh is
+ * not validated.
  * The sweeps' only scratch - one work-queue counter per sweep - is a fixed 4 KB array inside the library
  * that every GPU loading the library holds until the process exits.  Hence:
  *   - iters is limited to 1024 per call (LMS_ERR_ARG beyond, with a message);
  *   - the first call on a device looks up that array's address (and makes the driver load the library's
- *     device code), so make it once before any stream capture;
+ *     device code), so make it once before any stream capture; the address is kept for the process, so
+ *     after a cudaDeviceReset of a device this entry point must not be used on that device again;
  *   - every call shares the array: calls whose work overlaps on the GPU (other streams, other threads)
  *     race and give wrong results; serialise them.
  */
@@ -425,6 +445,20 @@ int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* 
 int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chunk, int32_t tile, int32_t ctas_per_sm);
 int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
                        int32_t* ctas_per_sm);
+
+/*
+ * Storage layout of a batch.  window = 0 stores every mesh in its ordering's sequence.  window > 0 (a
+ * multiple of 32, at most 65536) cuts each mesh's ordering sequence into runs of `window` consecutive
+ * positions and stores every run sorted by (boundary vertices first, then ascending neighbour count),
+ * stable inside equal keys: a vertex moves at most window - 1 places, and the threads of one warp get
+ * rows of about one length.  The ordering itself (lms_batch_get_permutation), the coordinates the batch
+ * holds and every Jacobi result are unchanged (Eq. 1 sums each row in its stored entry order, whatever
+ * the storage position).  Synchronous; rebuilds the tile tables and drops captured sweep graphs.
+ * lms_batch_autotune stores the batch under the ordering itself (window 0).  LMS_ERR_ARG (NULL, bad
+ * window), LMS_ERR_OOM, LMS_ERR_CUDA.
+ */
+int lms_batch_set_layout(lms_batch b, int32_t window);
+int lms_batch_get_layout(lms_batch b, int32_t* window);
 
 /* Ordering of mesh `mesh` of a batch ([n_mesh] new_to_old, local ids).  LMS_RANDOM uses seed + mesh. */
 int lms_batch_get_permutation(lms_batch b, int32_t mesh, int32_t* new_to_old);

@@ -47,6 +47,22 @@ def build(force=False):
     return _LIB
 
 
+_SRC_OMP = os.path.join(_HERE, "baseline_omp.c")
+_LIB_OMP = os.path.join(_HERE, "_build", "liblms_baseline_omp.so")
+
+
+def build_omp(force=False):
+    """Compile baseline_omp.c (the Jacobi sweep under an OpenMP static schedule, a timing baseline only)."""
+    if not force and os.path.exists(_LIB_OMP) and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC_OMP):
+        return _LIB_OMP
+    os.makedirs(os.path.dirname(_LIB_OMP), exist_ok=True)
+    tmp = _LIB_OMP + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                           "-shared", "-o", tmp, _SRC_OMP])
+    os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
 _P_I32 = ctypes.POINTER(ctypes.c_int32)
 _P_U8 = ctypes.POINTER(ctypes.c_uint8)
 _P_F64 = ctypes.POINTER(ctypes.c_double)
@@ -167,6 +183,28 @@ def smooth(row_ptr, col_idx, is_boundary, xy, iters, mode=JACOBI, seq=None, tri=
     if hist is not None:
         hist = hist[: done.value + 1]
     return out, done.value, hist
+
+
+_omp_handle = None
+
+
+def jacobi_omp(row_ptr, col_idx, is_boundary, xy, iters, threads=0):
+    """Timing baseline, not a parity reference: ``iters`` Jacobi sweeps with the vertex loop under an OpenMP
+    static schedule on ``threads`` host threads (0: all).  Returns (xy, threads used); equals ``smooth``'s
+    Jacobi result bit for bit."""
+    global _omp_handle
+    if _omp_handle is None:
+        lib = ctypes.CDLL(build_omp())
+        lib.bl_jacobi_omp.argtypes = [_I32, _P_I32, _P_I32, _P_U8, _P_F64, _I32, _I32]
+        lib.bl_jacobi_omp.restype = ctypes.c_int
+        _omp_handle = lib
+    row_ptr, col_idx, bnd = _i32(row_ptr), _i32(col_idx), _u8(is_boundary)
+    out = _f64(xy).reshape(-1, 2).copy()
+    used = _omp_handle.bl_jacobi_omp(len(row_ptr) - 1, _p(row_ptr, _P_I32), _p(col_idx, _P_I32), _p(bnd, _P_U8),
+                                     _p(out, _P_F64), int(iters), int(threads))
+    if used < 0:
+        raise RuntimeError("bl_jacobi_omp failed")
+    return out, used
 
 
 def order_random(n, seed):

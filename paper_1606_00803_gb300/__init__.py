@@ -80,6 +80,7 @@ _SIGS = {
     "lms_get_colors": ([_P, _P, _PI32], ctypes.c_int),
     "lms_get_csr": ([_P, _P, _P, _P], ctypes.c_int),
     "lms_last_stats": ([_P, _PD, _PD, _PD, _PD], ctypes.c_int),
+    "lms_last_error_stats": ([_P, _PD, _PD], ctypes.c_int),
     "lms_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_last_reorder_ms": ([_P, _PD, _PD], ctypes.c_int),
     "lms_set_inplace_split": ([_P, _I32], ctypes.c_int),
@@ -106,6 +107,9 @@ _SIGS = {
     "lms_batch_set_config": ([_P, _I32, _I32, _I32, _I32, _I32], ctypes.c_int),
     "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
     "lms_batch_get_permutation": ([_P, _I32, _P], ctypes.c_int),
+    "lms_batch_set_layout": ([_P, _I32], ctypes.c_int),
+    "lms_partition_meshes": ([_I32, _P, _I32, _P, _P], ctypes.c_int),
+    "lms_batch_get_layout": ([_P, _PI32], ctypes.c_int),
     "lms_batch_last_launches": ([_P, _PI64], ctypes.c_int),
     "lms_batch_destroy": ([_P], None),
 }
@@ -225,6 +229,15 @@ def order_host(row_ptr, col_idx, is_boundary, ordering, seed=0, q_v=None):
     _check(_lib().lms_order_host(n, _ptr(rp), _ptr(ci), _ptr(b), _ptr(q), int(ordering), seed & (2**64 - 1),
                                  _ptr(out)), "lms_order_host")
     return out
+
+
+def partition_meshes(n_vertices, ranks):
+    """lms_partition_meshes: (rank of each mesh, vertices per rank) - whole meshes balanced by vertex count."""
+    nv = _arr(n_vertices, np.int32)
+    rank_of, load = np.empty(len(nv), np.int32), np.empty(max(1, int(ranks)), np.int64)
+    _check(_lib().lms_partition_meshes(len(nv), _ptr(nv), int(ranks), _ptr(rank_of), _ptr(load)),
+           "lms_partition_meshes")
+    return rank_of, load
 
 
 def color_host(row_ptr, col_idx, is_boundary, new_to_old):
@@ -415,6 +428,12 @@ class Mesh:
                                      ctypes.byref(q1)), "lms_last_stats")
         return dict(max_disp=d.value, ms=ms.value, q_first=q0.value, q_last=q1.value)
 
+    def last_error_stats(self):
+        """lms_last_error_stats: (largest displacement of the last sweep, device ms) of the last smooth."""
+        d, ms = ctypes.c_double(), ctypes.c_double()
+        _check(_lib().lms_last_error_stats(self._handle(), ctypes.byref(d), ctypes.byref(ms)), "lms_last_error_stats")
+        return d.value, ms.value
+
     def last_launches(self):
         k = ctypes.c_int64()
         _check(_lib().lms_last_launches(self._handle(), ctypes.byref(k)), "lms_last_launches")
@@ -546,9 +565,22 @@ class Batch:
                "lms_batch_set_config")
 
     def autotune(self):
+        """lms_batch_autotune: the chosen launch configuration, with the storage layout's window."""
         v = [ctypes.c_int32() for _ in range(5)]
         _check(_lib().lms_batch_autotune(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_autotune")
-        return dict(zip(self._CFG, [x.value for x in v]))
+        cfg = dict(zip(self._CFG, [x.value for x in v]))
+        cfg["window"] = self.layout()
+        return cfg
+
+    def set_layout(self, window):
+        """lms_batch_set_layout: store each run of `window` ordering positions grouped by row length (0: the
+        ordering itself)."""
+        _check(_lib().lms_batch_set_layout(self._handle(), int(window)), "lms_batch_set_layout")
+
+    def layout(self):
+        w = ctypes.c_int32()
+        _check(_lib().lms_batch_get_layout(self._handle(), ctypes.byref(w)), "lms_batch_get_layout")
+        return w.value
 
     def last_launches(self):
         k = ctypes.c_int64()

@@ -671,6 +671,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.err = h->d_err;
         a.tile_cap = h->tile;
         a.e_cap = h->e_cap;
+        a.n_vertices = h->n;
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
         const int occ = std::max(1, lms::staged_occupancy(h->precision, mode != LMS_JACOBI, h->block, h->tile, h->e_cap));
@@ -1213,6 +1214,10 @@ int lms_last_stats(lms_handle h, double* max_disp, double* ms, double* q_first, 
     return LMS_OK;
 }
 
+int lms_last_error_stats(lms_handle h, double* max_disp, double* ms) {
+    return lms_last_stats(h, max_disp, ms, nullptr, nullptr);
+}
+
 int lms_last_launches(lms_handle h, int64_t* launches) {
     if (!h || !launches) return LMS_ERR_ARG;
     *launches = h->last_launches;
@@ -1310,7 +1315,8 @@ int lms_debug_checks(int32_t* enabled, uint64_t* violations, int32_t reset) {
     if (enabled) *enabled = lms::checks_enabled() ? 1 : 0;
     const unsigned long long v = lms::check_violations_kernels(reset != 0) +
                                  lms::check_violations_orderings(reset != 0) +
-                                 lms::check_violations_noalloc(reset != 0);
+                                 lms::check_violations_noalloc(reset != 0) +
+                                 lms::check_violations_staged(reset != 0);
     if (violations) *violations = v;
     return LMS_OK;
 }
@@ -1329,7 +1335,10 @@ struct lms_batch_s {
     int32_t k = 0;
     int64_t n_total = 0, n_int = 0, nnz_total = 0;
     std::vector<int64_t> voff;          // vertex offset of each mesh (k+1)
-    std::vector<int32_t> perm;          // global new_to_old
+    std::vector<int32_t> perm;          // global new_to_old of the storage layout
+    std::vector<int32_t> order_perm;    // global new_to_old of the ordering (lms_batch_get_permutation)
+    std::vector<uint8_t> bnd_store;     // boundary flag per storage position
+    int32_t window = 0;                 // degree-grouping window of the storage layout (0: the ordering)
     std::vector<int32_t> rp;            // relabelled global row offsets (host copy, for the tile table)
     std::vector<double> cs;             // per mesh (cx, cy, inv_s, s)
     int32_t *d_rp = nullptr, *d_ci = nullptr, *d_perm = nullptr, *d_item_mesh = nullptr, *d_queue = nullptr;
@@ -1507,6 +1516,7 @@ lms::StagedArgs batch_staged_args(lms_batch_s* b, int src, int dst, int slot) {
     a.queue = b->d_queue + slot;
     a.tile_cap = b->items_tile;
     a.e_cap = b->e_cap;
+    a.n_vertices = int32_t(b->n_total);
     a.err = b->d_err;
     return a;
 }
@@ -1600,11 +1610,109 @@ std::string autotune_key(lms_batch_s* b) {
         return l;
     };
     std::ostringstream os;
-    os << "v9|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    os << "v10|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
     std::string s = os.str();
     for (auto& c : s)
         if (c == ' ') c = '_';
     return s;
+}
+
+// Storage layout of the batch for degree-grouping window `window`: the ordering's sequence of each mesh
+// cut into runs of `window` consecutive positions (never crossing a mesh), each run stably sorted by
+// (boundary first, then ascending row length).  window = 0 keeps the ordering itself.  A warp's 32
+// threads then take rows of about one length, so a warp's row loop ends with its rows instead of
+// running to the longest of 32 mixed rows; positions move at most window - 1 places, so the ordering's
+// locality is kept.  Jacobi results do not depend on the storage order (rows keep their entry order).
+void layout_for_window(const lms_batch_s* b, int32_t window, const std::vector<int32_t>& deg_orig,
+                       const std::vector<uint8_t>& bnd_orig, std::vector<int32_t>& out) {
+    out = b->order_perm;
+    if (window <= 0) return;
+    std::vector<std::pair<int32_t, int32_t>> key;  // (class, position in the run): stable by position
+    for (int32_t m = 0; m < b->k; ++m)
+        for (int64_t t0 = b->voff[m]; t0 < b->voff[m + 1]; t0 += window) {
+            const int64_t t1 = std::min<int64_t>(t0 + window, b->voff[m + 1]);
+            key.clear();
+            for (int64_t i = t0; i < t1; ++i) {
+                const int32_t v = b->order_perm[i];
+                key.push_back({bnd_orig[v] ? -1 : deg_orig[v], int32_t(i)});
+            }
+            std::stable_sort(key.begin(), key.end(),
+                             [](const std::pair<int32_t, int32_t>& x, const std::pair<int32_t, int32_t>& y) {
+                                 return x.first < y.first;
+                             });
+            for (int64_t i = t0; i < t1; ++i) out[i] = b->order_perm[key[i - t0].second];
+        }
+}
+
+// Move the batch from its current storage layout to the layout of `window` on the device: rows gathered
+// with their entry order kept and ids renamed, boundary bits and row flags rebuilt, both position buffers
+// permuted (the coordinates the batch holds are kept); tile tables rebuilt and captured graphs dropped.
+int batch_relayout(lms_batch_s* b, int32_t window) {
+    if (window == b->window) return LMS_OK;
+    const int32_t N = int32_t(b->n_total);
+    const int64_t E = b->nnz_total;
+    std::vector<int32_t> deg_orig(N);
+    std::vector<uint8_t> bnd_orig(N);
+    for (int32_t i = 0; i < N; ++i) {
+        deg_orig[b->perm[i]] = b->rp[i + 1] - b->rp[i];
+        bnd_orig[b->perm[i]] = b->bnd_store[i];
+    }
+    std::vector<int32_t> np;
+    layout_for_window(b, window, deg_orig, bnd_orig, np);
+    // q[i] = current storage position of the vertex placed at i; qinv its inverse
+    std::vector<int32_t> inv_cur(N), q(N), qinv(N), rp_new(N + 1, 0);
+    std::vector<uint8_t> bnd_new(N);
+    for (int32_t i = 0; i < N; ++i) inv_cur[b->perm[i]] = i;
+    for (int32_t i = 0; i < N; ++i) {
+        q[i] = inv_cur[np[i]];
+        qinv[q[i]] = i;
+        rp_new[i + 1] = rp_new[i] + (b->rp[q[i] + 1] - b->rp[q[i]]);
+        bnd_new[i] = b->bnd_store[q[i]];
+    }
+    cudaStream_t s = b->stream;
+    LMS_CUDA(cudaStreamSynchronize(s));
+    Arena tmp;
+    tmp.al = b->arena.al;
+    tmp.stream = s;
+    int32_t *d_rp_old = nullptr, *d_ci_old = nullptr, *d_q = nullptr, *d_qinv = nullptr;
+    uint8_t* d_bnd_old = nullptr;
+    int rc = LMS_OK;
+    if ((rc = tmp.get(&d_rp_old, N + 1)) || (rc = tmp.get(&d_ci_old, std::max<int64_t>(1, E))) ||
+        (rc = tmp.get(&d_q, N)) || (rc = tmp.get(&d_qinv, N)) || (rc = tmp.get(&d_bnd_old, N))) {
+        tmp.release_all();
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_rp_old, b->rp.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_ci_old, b->d_ci, 4 * size_t(E), cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_q, q.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_qinv, qinv.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_bnd_old, b->bnd_store.data(), size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(b->d_rp, rp_new.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
+    if (!e) e = lms::launch_gather_rows(N, d_q, d_rp_old, d_ci_old, b->d_rp, b->d_ci, d_qinv, s);
+    if (!e) e = cudaMemsetAsync(b->d_bits, 0, 4 * size_t((N + 31) / 32), s);
+    if (!e) e = lms::launch_boundary_bits(N, d_q, d_bnd_old, b->d_bits, s);
+    if (!e) e = lms::launch_flag_boundary_rows(N, b->d_bits, b->d_rp, s);
+    for (int buf = 0; buf < 2 && !e; ++buf) {
+        e = lms::launch_gather_xy(LMS_FP32, N, d_q, b->d_xy[buf], b->d_xy[2], s);
+        if (!e) e = cudaMemcpyAsync(b->d_xy[buf], b->d_xy[2], sizeof(float2) * size_t(N), cudaMemcpyDeviceToDevice, s);
+    }
+    if (!e) e = cudaMemcpyAsync(b->d_perm, np.data(), 4 * size_t(N), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    tmp.release_all();
+    if (e) {
+        lms::set_error_detail(std::string("batch layout: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    b->rp.swap(rp_new);
+    b->perm.swap(np);
+    b->bnd_store.swap(bnd_new);
+    b->window = window;
+    b->graphs.clear();
+    b->items_tile = 0;
+    b->sell_sigma = 0;
+    LMS_TRY(batch_build_items(b, b->tile));
+    if (b->kernel == LMS_KERNEL_SELL) LMS_TRY(batch_build_sell(b, b->tile));
+    return LMS_OK;
 }
 
 }  // namespace
@@ -1823,6 +1931,9 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         return fail_orig(LMS_ERR_CUDA);
     }
     orig.release_all();
+    b->order_perm = b->perm;
+    b->bnd_store.resize(N);
+    for (int32_t i = 0; i < N; ++i) b->bnd_store[i] = bnd0[b->perm[i]];
     if ((rc = batch_build_items(b, b->tile))) return fail(rc);
     e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_fixed, b->d_xy[0],
                                   b->d_xy[1], b->d_cs, b->d_err + 1, s);
@@ -1887,23 +1998,26 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string kk;
-            int kn, bl, ch, ti, cp;
-            if ((is >> kk >> kn >> bl >> ch >> ti >> cp) && kk == key && lms_batch_set_config(b, kn, bl, ch, ti, cp) == LMS_OK)
+            int kn, bl, ch, ti, cp, wi;
+            if ((is >> kk >> kn >> bl >> ch >> ti >> cp >> wi) && kk == key && batch_relayout(b, wi) == LMS_OK &&
+                lms_batch_set_config(b, kn, bl, ch, ti, cp) == LMS_OK)
                 return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
         }
     }
     struct Cand {
-        int kernel, block, chunk, tile;
+        int kernel, block, chunk, tile, window;
     };
+    // the storage layout is the ordering itself: windows grouped by row length (lms_batch_set_layout) were
+    // 2-7% slower on every configuration of the 512-mesh batch (a warp's gathers spread over more lines)
     std::vector<Cand> cands;
     for (int blk : {128, 256, 512})
         for (int ch : {1, 2, 3, 4, 5, 6, 8})
-            for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_DIRECT, blk, ch, ti});
+            for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_DIRECT, blk, ch, ti, 0});
     for (int blk : {128, 256})
-        for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti});
+        for (int ti : {128, 256, 512}) cands.push_back({LMS_KERNEL_STAGED, blk, 1, ti, 0});
     for (int ti : {512, 1024, 2048})  // sigma outermost: the SELL tables are rebuilt once per sigma
         for (int blk : {128, 256})
-            for (int ch : {4, 8}) cands.push_back({LMS_KERNEL_SELL, blk, ch, ti});
+            for (int ch : {4, 8}) cands.push_back({LMS_KERNEL_SELL, blk, ch, ti, 0});
     cudaStream_t s = b->stream;
     cudaEvent_t e0, e1;
     LMS_CUDA(cudaEventCreate(&e0));
@@ -1914,6 +2028,7 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
     const bool verbose = std::getenv("LMS_AUTOTUNE_VERBOSE") != nullptr;
     LMS_TRY(ensure_queue(b, reps + 2));
     for (const Cand& c : cands) {
+        if (batch_relayout(b, c.window) != LMS_OK) continue;
         if (lms_batch_set_config(b, c.kernel, c.block, c.chunk, c.tile, 0) != LMS_OK) continue;
         const int grid = batch_grid(b);
         // reads buffer cur, writes the scratch buffer: the batch's positions are untouched
@@ -1931,8 +2046,8 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
             ms = std::min(ms, t);
         }
         if (verbose)
-            std::fprintf(stderr, "[lms autotune] kernel=%d block=%d chunk=%d tile=%d grid=%d: %.4f ms/sweep\n", c.kernel,
-                         c.block, c.chunk, c.tile, grid, ms / reps);
+            std::fprintf(stderr, "[lms autotune] kernel=%d block=%d chunk=%d tile=%d window=%d grid=%d: %.4f ms/sweep\n",
+                         c.kernel, c.block, c.chunk, c.tile, c.window, grid, ms / reps);
         if (ms < best) {
             best = ms;
             win = c;
@@ -1940,10 +2055,12 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    LMS_TRY(batch_relayout(b, win.window));
     LMS_TRY(lms_batch_set_config(b, win.kernel, win.block, win.chunk, win.tile, 0));
     if (cache) {
         std::ofstream f(cache, std::ios::app);
-        f << key << " " << win.kernel << " " << win.block << " " << win.chunk << " " << win.tile << " 0\n";
+        f << key << " " << win.kernel << " " << win.block << " " << win.chunk << " " << win.tile << " 0 " << win.window
+          << "\n";
     }
     return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
 }
@@ -2206,10 +2323,21 @@ int lms_batch_last_launches(lms_batch b, int64_t* launches) {
     return LMS_OK;
 }
 
+int lms_batch_set_layout(lms_batch b, int32_t window) {
+    if (!b || window < 0 || window > 65536 || (window % 32) != 0) return LMS_ERR_ARG;
+    return batch_relayout(b, window);
+}
+
+int lms_batch_get_layout(lms_batch b, int32_t* window) {
+    if (!b || !window) return LMS_ERR_ARG;
+    *window = b->window;
+    return LMS_OK;
+}
+
 int lms_batch_get_permutation(lms_batch b, int32_t mesh, int32_t* new_to_old) {
     if (!b || !new_to_old || mesh < 0 || mesh >= b->k) return LMS_ERR_ARG;
     const int64_t v0 = b->voff[mesh], nv = b->voff[mesh + 1] - v0;
-    for (int64_t i = 0; i < nv; ++i) new_to_old[i] = int32_t(b->perm[v0 + i] - v0);
+    for (int64_t i = 0; i < nv; ++i) new_to_old[i] = int32_t(b->order_perm[v0 + i] - v0);
     return LMS_OK;
 }
 

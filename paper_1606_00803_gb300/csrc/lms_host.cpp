@@ -31,6 +31,7 @@
 #include <new>
 #include <thread>
 #include <deque>
+#include <queue>
 #include <vector>
 
 #include "lms_internal.h"
@@ -460,13 +461,16 @@ int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, c
 // the order is two stable counting sorts (tiles by colour, then each tile's vertices by colour).
 int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                 const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
-                int32_t* order, int32_t* n_order) {
+                int32_t* order, int32_t* n_order, int32_t* vertex_colour, int32_t* nvertex_colours) {
     if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !new_to_old || tile < 1 || !tile_colour ||
         !ntile_colours || !order || !n_order)
         return LMS_ERR_ARG;
-    std::vector<int32_t> colour(n);
+    std::vector<int32_t> own;
+    if (!vertex_colour) own.resize(n);
+    int32_t* colour = vertex_colour ? vertex_colour : own.data();
     int32_t nc = 0;
-    if (int rc = colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour.data(), &nc)) return rc;
+    if (int rc = colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour, &nc)) return rc;
+    if (nvertex_colours) *nvertex_colours = nc;
     std::vector<int32_t> pos(n);
     for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
     const int32_t ntiles = static_cast<int32_t>((static_cast<int64_t>(n) + tile - 1) / tile);
@@ -522,10 +526,10 @@ int block_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
     const int32_t ntiles = static_cast<int32_t>((static_cast<int64_t>(n) + tile - 1) / tile);
     std::vector<int32_t> tile_colour(ntiles), order(n), colour(n);
     int32_t ntc = 0, m = 0, nc = 0;
+    // the vertex colouring block_order computes is the one the colour groups need
     if (int rc = block_order(n, row_ptr, col_idx, is_boundary, new_to_old, tile, tile_colour.data(), &ntc,
-                             order.data(), &m))
+                             order.data(), &m, colour.data(), &nc))
         return rc;
-    if (int rc = colour_vertices(n, row_ptr, col_idx, is_boundary, new_to_old, colour.data(), &nc)) return rc;
     nc = std::max(1, nc);
     std::vector<int32_t> pos(n);
     for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
@@ -631,6 +635,32 @@ int lms_reuse_profile(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
     } catch (const std::bad_alloc&) {
         return LMS_ERR_OOM;
     }
+}
+
+int lms_partition_meshes(int32_t k, const int32_t* n_vertices, int32_t ranks, int32_t* rank_of, int64_t* load) {
+    if (k < 1 || ranks < 1 || !n_vertices || !rank_of) return LMS_ERR_ARG;
+    for (int32_t m = 0; m < k; ++m)
+        if (n_vertices[m] < 1) return LMS_ERR_ARG;
+    std::vector<int32_t> by_size(k);
+    for (int32_t m = 0; m < k; ++m) by_size[m] = m;
+    std::stable_sort(by_size.begin(), by_size.end(),
+                     [&](int32_t a, int32_t b) { return n_vertices[a] > n_vertices[b]; });
+    // least-loaded rank first; ties to the lower rank
+    using Slot = std::pair<int64_t, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int32_t r = 0; r < ranks; ++r) heap.push({0, r});
+    std::vector<int64_t> tot(ranks, 0);
+    for (int32_t m : by_size) {
+        Slot s = heap.top();
+        heap.pop();
+        rank_of[m] = s.second;
+        s.first += n_vertices[m];
+        tot[s.second] = s.first;
+        heap.push(s);
+    }
+    if (load)
+        for (int32_t r = 0; r < ranks; ++r) load[r] = tot[r];
+    return LMS_OK;
 }
 
 }  // extern "C"

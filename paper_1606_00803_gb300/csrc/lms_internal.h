@@ -27,10 +27,12 @@ int order_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, co
 int colour_vertices(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                     const int32_t* new_to_old, int32_t* colour, int32_t* ncolours);
 
-// Block order of the in-place sweep (see lms_block_order in lms.h).
+// Block order of the in-place sweep (see lms_block_order in lms.h).  vertex_colour ([n], by original id)
+// and nvertex_colours, when given, receive the first-fit vertex colouring the order uses.
 int block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                 const int32_t* new_to_old, int32_t tile, int32_t* tile_colour, int32_t* ntile_colours,
-                int32_t* order, int32_t* n_order);
+                int32_t* order, int32_t* n_order, int32_t* vertex_colour = nullptr,
+                int32_t* nvertex_colours = nullptr);
 
 // Tables of a block Gauss-Seidel sweep (LMS_BLOCK_GS) for storage order new_to_old: verts = storage
 // positions of the interior vertices in block order; per listed tile (a tile holding interior vertices,
@@ -117,6 +119,7 @@ struct StagedArgs {
     int32_t* queue;                // tile counter of this launch (zeroed before it)
     int32_t tile_cap;              // max vertices per tile
     int32_t e_cap;                 // max CSR entries per tile
+    int32_t n_vertices;            // vertices addressable by col_idx (bounds checks of debug builds)
     const DevState* state;         // stop flag (NULL: never stop)
     unsigned long long* disp2;     // max squared displacement (NULL: off)
     const double* recip;           // FP64 reciprocal table
@@ -169,6 +172,7 @@ int block_rdr_max_degree();  // rows longer than this need the host implementati
 unsigned long long check_violations_kernels(bool reset);
 unsigned long long check_violations_orderings(bool reset);
 unsigned long long check_violations_noalloc(bool reset);
+unsigned long long check_violations_staged(bool reset);
 bool checks_enabled();
 
 // Launchers (all asynchronous on `stream`; return cudaError_t of the launch).

@@ -9,6 +9,7 @@
 // device array, so each GPU that loads the library holds it (4 KB) until the
 // process exits.
 #include <algorithm>
+#include <cstdint>
 #include <mutex>
 
 #include "lms_device.cuh"
@@ -27,8 +28,9 @@ std::mutex g_setup_mu;
 int32_t* g_queue_addr[kMaxDevices] = {};
 int g_sm_count[kMaxDevices] = {};
 
-// Eq. 1 on every interior vertex (sequential FP64 sums in row order, IEEE division), boundary
-// vertices copied; CTAs pull tiles of kNoAllocTile vertices from *queue.
+// Every interior vertex moves to the mean of its neighbours' positions (FP64 sums in stored row order,
+// then one IEEE division by the neighbour count); boundary vertices are copied.  CTAs pull tiles of
+// kNoAllocTile vertices from *queue.
 __global__ void __launch_bounds__(kNoAllocTile) k_jacobi_noalloc(int32_t n, const int32_t* __restrict__ row_ptr,
                                                                  const int32_t* __restrict__ col_idx,
                                                                  const uint8_t* __restrict__ is_boundary,
@@ -62,7 +64,9 @@ __global__ void __launch_bounds__(kNoAllocTile) k_jacobi_noalloc(int32_t n, cons
     }
 }
 
-// Address of the counters on the current device (first call on a device looks it up).
+// Address of the counters on the current device.  The first call on a device looks it up and caches it;
+// a cudaDeviceReset of that device ends the context the array lived in, so the cached address is stale
+// afterwards (the header tells callers not to use this entry point on a device after a reset).
 int noalloc_setup(int32_t** queue, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -105,8 +109,15 @@ LMS_CHECK_ACCESSOR(check_violations_noalloc)
 extern "C" int lms_jacobi_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                   const uint8_t* is_boundary, double* xy, double* xy_tmp, int32_t iters,
                                   void* cuda_stream) {
-    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !xy || !xy_tmp || xy == xy_tmp || iters < 0)
-        return LMS_ERR_ARG;
+    if (n <= 0 || !row_ptr || !col_idx || !is_boundary || !xy || !xy_tmp || iters < 0) return LMS_ERR_ARG;
+    {  // the two position buffers must not share a byte: [xy, xy + 2n) and [xy_tmp, xy_tmp + 2n)
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(xy), b0 = reinterpret_cast<uintptr_t>(xy_tmp);
+        const uintptr_t len = sizeof(double) * 2 * uintptr_t(n);
+        if (a0 < b0 + len && b0 < a0 + len) {
+            lms::set_error_detail("lms_jacobi_noalloc: xy and xy_tmp overlap");
+            return LMS_ERR_ARG;
+        }
+    }
     if (iters > kNoAllocMaxSweeps) {
         lms::set_error_detail("lms_jacobi_noalloc runs at most 1024 sweeps per call");
         return LMS_ERR_ARG;
@@ -119,7 +130,8 @@ extern "C" int lms_jacobi_noalloc(int32_t n, const int32_t* row_ptr, const int32
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the counters keep the previous call's values: clear the ones this call uses
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t) * size_t(iters), s);
-    const int grid = std::max(1, std::min(8 * sms, (n + kNoAllocTile - 1) / kNoAllocTile));
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(8 * int64_t(sms), (int64_t(n) + kNoAllocTile - 1) /
+                                                                                    kNoAllocTile)));
     double2* a = reinterpret_cast<double2*>(xy);
     double2* b = reinterpret_cast<double2*>(xy_tmp);
     for (int32_t k = 0; k < iters && e == cudaSuccess; ++k) {

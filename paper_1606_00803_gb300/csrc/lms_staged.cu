@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(256) k_sweep_staged(StagedArgs a) {
                 for (int g = 0; g < kGather; ++g) {
                     const int32_t k = k0 + g * static_cast<int32_t>(blockDim.x);
                     u[g] = k < E ? ci[k] : -1;
+                    if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
                 }
 #pragma unroll
                 for (int g = 0; g < kGather; ++g)
@@ -316,6 +317,8 @@ cudaError_t launch_sweep_staged(int precision, bool in_place, const StagedArgs& 
     return in_place ? launch_t<false, true>(a, grid, block, smem, stream)
                     : launch_t<false, false>(a, grid, block, smem, stream);
 }
+
+LMS_CHECK_ACCESSOR(check_violations_staged)
 
 int staged_occupancy(int precision, bool in_place, int block, int32_t tile_cap, int32_t e_cap) {
     const size_t smem = staged_smem_bytes(precision, tile_cap, e_cap);

@@ -303,3 +303,44 @@ int main(void) {
                     "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
     out = subprocess.run([str(exe)], stdout=subprocess.PIPE, check=True).stdout.decode().split()
     assert out == ["0", "1", "2", "3"]
+
+
+def test_partition_meshes_covers_and_balances():
+    """lms_partition_meshes: every mesh on one rank, loads add up, the spread is at most the largest mesh,
+    and on tiny inputs the makespan is within Graham's LPT bound (4/3 - 1/(3r)) of the optimum found by
+    brute force."""
+    import itertools
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        k = int(rng.integers(1, 9))
+        ranks = int(rng.integers(1, 5))
+        sizes = rng.integers(1, 50, size=k).astype(np.int32)
+        rank_of, load = lms.partition_meshes(sizes, ranks)
+        assert rank_of.min() >= 0 and rank_of.max() < ranks
+        assert [int(sizes[rank_of == r].sum()) for r in range(ranks)] == list(load)
+        assert load.max() - load.min() <= sizes.max()
+        best = min(max(sum(int(sizes[i]) for i in range(k) if a[i] == r) for r in range(ranks))
+                   for a in itertools.product(range(ranks), repeat=k))
+        assert load.max() <= (4 / 3 - 1 / (3 * ranks)) * best + 1e-9
+        again, _ = lms.partition_meshes(sizes, ranks)
+        assert np.array_equal(again, rank_of)
+    # a large batch like the benchmark's: 512 sizes, 8 ranks
+    sizes = rng.integers(1000, 200000, size=512).astype(np.int32)
+    rank_of, load = lms.partition_meshes(sizes, 8)
+    assert load.max() - load.min() <= sizes.max() and load.sum() == sizes.sum()
+    for bad in (([], 2), ([3, 0], 2), ([3, 4], 0)):
+        with pytest.raises(lms.LmsError):
+            lms.partition_meshes(np.asarray(bad[0], np.int32), bad[1])
+
+
+def test_noalloc_rejects_overlapping_buffers_before_device_work():
+    """lms_jacobi_noalloc checks its arguments before any CUDA call: position buffers that share a byte are
+    rejected (the addresses below are never dereferenced)."""
+    fn = lms._lib().lms_jacobi_noalloc
+    n = 100
+    base = 0x10000000
+    for other in (base, base + 8, base + 16 * n - 8, base - 16 * n + 8):
+        assert fn(n, 1, 1, 1, base, other, 1, None) == -1
+        assert "overlap" in lms._lib().lms_last_error_detail().decode()
+    assert fn(0, 1, 1, 1, base, base + 16 * n, 1, None) == -1
+    assert fn(n, 1, 1, 1, base, base + 16 * n, -1, None) == -1

@@ -192,6 +192,7 @@ def test_boundary_fixed_and_displacement(mesh_mid, precision):
         g.smooth(1)
         x31 = g.coords()
         st = g.last_stats()
+        assert g.last_error_stats() == (st["max_disp"], st["ms"])  # the boundary's lms_last_error_stats
     assert np.array_equal(x31[b], m["xy"][b])  # FP32 returns the stored FP64 boundary values
     want = np.sqrt(((x31 - x30) ** 2).sum(axis=1)).max()
     assert abs(st["max_disp"] - want) <= (1e-15 if precision == lms.FP64 else 1e-6) * diag(m) + 1e-12 * want

@@ -498,3 +498,15 @@ def test_plausible_mistakes_fail_the_pins():
     assert np.abs(got - ref).max() > 1e-6
     q = oracle.triangle_quality(np.array([[0, 1, 2]], np.int32), np.array([[0, 0], [4, 0], [0, 3]], np.float64))
     assert q[0] != 5 / 3
+
+
+def test_openmp_timing_baseline_equals_oracle_jacobi():
+    """The all-core timing baseline (OpenMP static schedule over vertices) runs the oracle's Eq. 1
+    arithmetic per vertex, so its Jacobi result equals the single-thread oracle bit for bit at any thread
+    count."""
+    m = meshgen.generate(37, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=77)
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 13)
+    for threads in (1, 3, 0):
+        got, used = oracle.jacobi_omp(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 13, threads)
+        assert used >= 1 and (threads == 0 or used == threads)
+        assert np.array_equal(got, want)
