@@ -780,8 +780,7 @@ def run_ours(args, dist):
                          "from their initial coordinates (FP32 with Kahan sums vs the FP64 oracle; bound 2e-6)"
                          % (k, SWEEPS_PER_STEP)) if err is not None else "computed at N = 1 only",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "kernel": {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"]}.get(
-                             cfg["kernel"], "k_batch_sweep<%d>" % cfg["chunk"]),
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": kernel_name(cfg),
                          "algorithmic_bytes_per_sweep": ab, "sweep_ms": sweep_ms,
                          "launches_per_sweep": launches_per_step // SWEEPS_PER_STEP,
                          "unit_note": "one sweep of the whole batch = one launch per mesh chain (two chains run "
@@ -801,6 +800,13 @@ def run_ours(args, dist):
     b.close()
 
 
+def kernel_name(cfg):
+    import paper_1606_00803_gb300 as lms
+    return {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"],
+            lms.KERNEL_PACKED: "k_batch_sweep_packed<%d>" % cfg["chunk"]}.get(cfg["kernel"],
+                                                                              "k_batch_sweep<%d>" % cfg["chunk"])
+
+
 def _braced_block(text, start):
     """text[start:] up to the brace that closes the first opening brace after start."""
     i = text.index("{", start)
@@ -812,23 +818,29 @@ def _braced_block(text, start):
     raise ValueError("unbalanced braces")
 
 
-def kernel_source_digest():
-    """sha256 over the source of the batched sweep kernel (k_batch_sweep), its argument struct and the
-    device helpers it calls (the bounds-check macros, the Kahan sum, the FP32 mean, the displacement
-    maximum): any change to them makes recorded counters stale."""
+def kernel_source_digest(kernel="k_batch_sweep"):
+    """sha256 over the source of a batched sweep kernel (k_batch_sweep or k_batch_sweep_packed), its argument
+    struct, the row-order kernel that lays out the batch's rows and the device helpers the sweep calls (the
+    bounds-check macros, the Kahan sum, the FP32 mean, the displacement maximum): any change to them makes
+    recorded counters stale."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1606_00803_gb300", "csrc")
     kernels = open(os.path.join(csrc, "lms_kernels.cu")).read()
     internal = open(os.path.join(csrc, "lms_internal.h")).read()
     device = open(os.path.join(csrc, "lms_device.cuh")).read()
     checks = device.index("#ifdef LMS_CHECKS")
-    parts = [
-        _braced_block(kernels, kernels.index("template <int CHUNK, bool EXTRAS>\n__global__ void __launch_bounds__(512) k_batch_sweep")),
-        _braced_block(internal, internal.index("struct SweepArgs {")),
-        device[checks:device.index("#endif", checks)],
-    ] + [_braced_block(device, device.index(sig)) for sig in (
-        "__device__ __forceinline__ float mean_f32(", "__device__ __forceinline__ void kahan_add(",
-        "__device__ __forceinline__ void max_to(", "__device__ __forceinline__ void record_disp(")]
+    if kernel.startswith("k_batch_sweep_packed"):
+        body = _braced_block(kernels, kernels.index("template <int CHUNK>\n__global__ void __launch_bounds__(512) "
+                                                    "k_batch_sweep_packed"))
+        args = internal[internal.index("constexpr int kPackedDegreeShift"):internal.index("cudaError_t launch_batch_sweep_packed")]
+    else:
+        body = _braced_block(kernels, kernels.index("template <int CHUNK, bool EXTRAS>\n__global__ void __launch_bounds__(512) k_batch_sweep"))
+        args = _braced_block(internal, internal.index("struct SweepArgs {"))
+    parts = [body, args, _braced_block(kernels, kernels.index("__global__ void k_sort_rows_far_first(")),
+             device[checks:device.index("#endif", checks)],
+             ] + [_braced_block(device, device.index(sig)) for sig in (
+                 "__device__ __forceinline__ float mean_f32(", "__device__ __forceinline__ void kahan_add(",
+                 "__device__ __forceinline__ void max_to(", "__device__ __forceinline__ void record_disp(")]
     h = hashlib.sha256()
     for p in parts:
         h.update(p.encode() + b"\0")
@@ -843,7 +855,7 @@ def load_traffic(kernel, config, chains):
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_digest") != kernel_source_digest() or t.get("kernel") != kernel:
+    if t.get("kernel") != kernel or t.get("source_digest") != kernel_source_digest(kernel):
         return None
     if any(t.get("config", {}).get(k) != config.get(k) for k in ("kernel", "block", "chunk", "tile")):
         return None

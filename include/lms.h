@@ -99,6 +99,10 @@ extern "C" {
 #define LMS_KERNEL_SELL 2   /* batched only: SELL-C-sigma work layout - inside every tile the interior vertices
                                sorted by degree into slices of 32 whose neighbour ids are stored
                                column-major; one lane per slot, coalesced id loads, no row offsets */
+#define LMS_KERNEL_PACKED 3 /* batched only: one thread per vertex; one 32-bit word per vertex packs its row's
+                               offset within its mesh, its neighbour count and its boundary flag, so a
+                               thread learns its row from one load; needs meshes of fewer than 2^22 CSR
+                               entries and rows of at most 63 entries */
 
 /* where the FP64 sweep's arithmetic runs (lms_set_fp64_arith); every choice gives the IEEE
    round-to-nearest sums and quotients, so results are identical */
@@ -445,6 +449,16 @@ int lms_batch_get_config(lms_batch b, int32_t* kernel, int32_t* block, int32_t* 
 int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chunk, int32_t tile, int32_t ctas_per_sm);
 int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
                        int32_t* ctas_per_sm);
+
+/*
+ * Chains of the sweep graph of lms_batch_smooth: the meshes are cut into `chains` runs of whole meshes
+ * with about equal vertex counts, and each run's sweeps form an independent chain of launches in one
+ * CUDA graph, so the end of one chain's sweep overlaps the other chains' work.  1 to 8 (default 2; the
+ * SELL kernel always uses 1); results do not depend on it.  lms_batch_autotune times 1 to 4 chains on
+ * the chosen launch configuration and keeps the fastest.  [no device work]  LMS_ERR_ARG.
+ */
+int lms_batch_set_chains(lms_batch b, int32_t chains);
+int lms_batch_get_chains(lms_batch b, int32_t* chains);
 
 /*
  * Storage layout of a batch.  window = 0 stores every mesh in its ordering's sequence.  window > 0 (a

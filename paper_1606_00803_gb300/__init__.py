@@ -22,7 +22,7 @@ import numpy as np
 from . import _build
 
 FP64, FP32 = 0, 1
-KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL = 0, 1, 2
+KERNEL_DIRECT, KERNEL_STAGED, KERNEL_SELL, KERNEL_PACKED = 0, 1, 2, 3
 ORI, RANDOM, BFS, RDR, RBFS, BRDR = 0, 1, 2, 3, 4, 5
 BRDR_BLOCK = 4096  # LMS_BRDR_BLOCK
 JACOBI, COLORED_GS, INPLACE_STATIC, BLOCK_GS = 0, 1, 2, 3
@@ -108,6 +108,8 @@ _SIGS = {
     "lms_batch_autotune": ([_P, _PI32, _PI32, _PI32, _PI32, _PI32], ctypes.c_int),
     "lms_batch_get_permutation": ([_P, _I32, _P], ctypes.c_int),
     "lms_batch_set_layout": ([_P, _I32], ctypes.c_int),
+    "lms_batch_set_chains": ([_P, _I32], ctypes.c_int),
+    "lms_batch_get_chains": ([_P, _PI32], ctypes.c_int),
     "lms_partition_meshes": ([_I32, _P, _I32, _P, _P], ctypes.c_int),
     "lms_batch_get_layout": ([_P, _PI32], ctypes.c_int),
     "lms_batch_last_launches": ([_P, _PI64], ctypes.c_int),
@@ -570,7 +572,17 @@ class Batch:
         _check(_lib().lms_batch_autotune(self._handle(), *[ctypes.byref(x) for x in v]), "lms_batch_autotune")
         cfg = dict(zip(self._CFG, [x.value for x in v]))
         cfg["window"] = self.layout()
+        cfg["chains"] = self.chains()
         return cfg
+
+    def set_chains(self, chains):
+        """lms_batch_set_chains: parallel chains of sweeps in the smoothing graph (results do not change)."""
+        _check(_lib().lms_batch_set_chains(self._handle(), int(chains)), "lms_batch_set_chains")
+
+    def chains(self):
+        c = ctypes.c_int32()
+        _check(_lib().lms_batch_get_chains(self._handle(), ctypes.byref(c)), "lms_batch_get_chains")
+        return c.value
 
     def set_layout(self, window):
         """lms_batch_set_layout: store each run of `window` ordering positions grouped by row length (0: the

@@ -1347,6 +1347,9 @@ struct lms_batch_s {
     uint32_t* d_bits = nullptr;
     int2* d_items = nullptr;
     int4* d_items4 = nullptr;           // (first vertex, end vertex, first entry, end entry)
+    int32_t* d_item_ebase = nullptr;    // per tile: first CSR entry of the tile's mesh (packed kernel)
+    int32_t* d_rw = nullptr;            // packed row words (LMS_KERNEL_PACKED), null when the batch does not fit
+    bool packed_ok = false;             // every mesh < 2^22 entries and every row <= kMaxPackedDegree entries
     int32_t e_cap = 0;                  // max CSR entries of a tile
     // SELL-C-sigma work layout (built on demand for the current tile size)
     int32_t* d_sell_col = nullptr;
@@ -1364,6 +1367,7 @@ struct lms_batch_s {
     int32_t queue_slots = 0;
     // launch configuration
     int kernel = LMS_KERNEL_DIRECT, block = 128, chunk = 4, tile = 512, ctas_per_sm = 0;
+    int chains = 2;                     // parallel chains of sweeps in a lms_batch_smooth graph
     bool configured = false;
     int32_t n_items = 0;
     int items_tile = 0;                 // tile size the item table was built for
@@ -1410,7 +1414,7 @@ int batch_build_items(lms_batch_s* b, int tile) {
     if (b->items_tile == tile) return LMS_OK;
     std::vector<int2> items;
     std::vector<int4> items4;
-    std::vector<int32_t> im;
+    std::vector<int32_t> im, ieb;
     int32_t e_cap = 0;
     for (int32_t m = 0; m < b->k; ++m)
         for (int64_t v = b->voff[m]; v < b->voff[m + 1]; v += tile) {
@@ -1419,8 +1423,11 @@ int batch_build_items(lms_batch_s* b, int tile) {
             items4.push_back(make_int4(va, vb, b->rp[va], b->rp[vb]));
             e_cap = std::max(e_cap, b->rp[vb] - b->rp[va]);
             im.push_back(m);
+            ieb.push_back(b->rp[b->voff[m]]);
         }
     if (int64_t(items.size()) > b->items_capacity) return LMS_ERR_STATE;
+    LMS_CUDA(cudaMemcpyAsync(b->d_item_ebase, ieb.data(), sizeof(int32_t) * ieb.size(), cudaMemcpyHostToDevice,
+                             b->stream));
     LMS_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream));
     LMS_CUDA(cudaMemcpyAsync(b->d_items4, items4.data(), sizeof(int4) * items4.size(), cudaMemcpyHostToDevice,
                              b->stream));
@@ -1504,6 +1511,44 @@ int batch_build_sell(lms_batch_s* b, int sigma) {
     return LMS_OK;
 }
 
+// Packed row words of the current layout (LMS_KERNEL_PACKED): offset of the row within its mesh's entries,
+// neighbour count, boundary flag.  Leaves packed_ok false (and the kernel unavailable) when a mesh has
+// 2^22 entries or more or a row more than kMaxPackedDegree entries.
+int batch_build_row_words(lms_batch_s* b) {
+    b->packed_ok = false;
+    const int32_t N = int32_t(b->n_total);
+    std::vector<int32_t> rw(N);
+    for (int32_t m = 0; m < b->k; ++m) {
+        const int32_t v0 = int32_t(b->voff[m]), v1 = int32_t(b->voff[m + 1]);
+        if (int64_t(b->rp[v1]) - b->rp[v0] > lms::kPackedOffsetMask) return LMS_OK;
+        for (int32_t v = v0; v < v1; ++v) {
+            const int32_t d = b->rp[v + 1] - b->rp[v];
+            if (d > lms::kMaxPackedDegree) return LMS_OK;
+            rw[v] = (b->rp[v] - b->rp[v0]) | (d << lms::kPackedDegreeShift) |
+                    (b->bnd_store[v] ? int32_t(0x80000000u) : 0);
+        }
+    }
+    if (!b->d_rw) LMS_TRY(b->arena.get(&b->d_rw, std::max(1, N)));
+    LMS_CUDA(cudaMemcpyAsync(b->d_rw, rw.data(), sizeof(int32_t) * size_t(N), cudaMemcpyHostToDevice, b->stream));
+    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    b->packed_ok = true;
+    return LMS_OK;
+}
+
+lms::PackedArgs batch_packed_args(lms_batch_s* b, int src, int dst, int slot) {
+    lms::PackedArgs a{};
+    a.row_words = b->d_rw;
+    a.col_idx = b->d_ci;
+    a.src = b->d_xy[src];
+    a.dst = b->d_xy[dst];
+    a.items = b->d_items;
+    a.items_ebase = b->d_item_ebase;
+    a.n_items = b->n_items;
+    a.queue = b->d_queue + slot;
+    a.n_vertices = int32_t(b->n_total);
+    return a;
+}
+
 lms::StagedArgs batch_staged_args(lms_batch_s* b, int src, int dst, int slot) {
     lms::StagedArgs a{};
     a.row_ptr = b->d_rp;
@@ -1538,6 +1583,7 @@ SweepArgs batch_args(lms_batch_s* b, int src, int dst, int slot) {
 
 int batch_occupancy(lms_batch_s* b) {
     if (b->kernel == LMS_KERNEL_SELL) return lms::batch_sell_occupancy(b->block, b->chunk);
+    if (b->kernel == LMS_KERNEL_PACKED) return lms::batch_packed_occupancy(b->block, b->chunk);
     if (b->kernel == LMS_KERNEL_STAGED)
         return lms::staged_occupancy(LMS_FP32, false, b->block, b->items_tile, b->e_cap);
     return lms::batch_sweep_occupancy(b->block, b->chunk);
@@ -1552,6 +1598,13 @@ int batch_issue_range(lms_batch_s* b, int src, int dst, int slot, int grid, cuda
         a.items += i0;
         a.n_items = i1 - i0;
         return check_launch(lms::launch_sweep_staged(LMS_FP32, false, a, grid, b->block, s), "staged_sweep");
+    }
+    if (b->kernel == LMS_KERNEL_PACKED) {
+        lms::PackedArgs a = batch_packed_args(b, src, dst, slot);
+        a.items += i0;
+        a.items_ebase += i0;
+        a.n_items = i1 - i0;
+        return check_launch(lms::launch_batch_sweep_packed(a, b->block, b->chunk, grid, s), "batch_sweep_packed");
     }
     SweepArgs a = batch_args(b, src, dst, slot);
     a.items += i0;
@@ -1576,6 +1629,10 @@ int batch_issue(lms_batch_s* b, int src, int dst, int slot, int grid, cudaStream
         return check_launch(lms::launch_sweep_staged(LMS_FP32, false, batch_staged_args(b, src, dst, slot), grid,
                                                      b->block, s),
                             "staged_sweep");
+    if (b->kernel == LMS_KERNEL_PACKED)
+        return check_launch(lms::launch_batch_sweep_packed(batch_packed_args(b, src, dst, slot), b->block, b->chunk,
+                                                           grid, s),
+                            "batch_sweep_packed");
     return check_launch(lms::launch_batch_sweep(batch_args(b, src, dst, slot), b->block, b->chunk, grid, s),
                         "batch_sweep");
 }
@@ -1610,7 +1667,7 @@ std::string autotune_key(lms_batch_s* b) {
         return l;
     };
     std::ostringstream os;
-    os << "v10|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    os << "v11|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
     std::string s = os.str();
     for (auto& c : s)
         if (c == ' ') c = '_';
@@ -1711,7 +1768,9 @@ int batch_relayout(lms_batch_s* b, int32_t window) {
     b->items_tile = 0;
     b->sell_sigma = 0;
     LMS_TRY(batch_build_items(b, b->tile));
+    LMS_TRY(batch_build_row_words(b));
     if (b->kernel == LMS_KERNEL_SELL) LMS_TRY(batch_build_sell(b, b->tile));
+    if (b->kernel == LMS_KERNEL_PACKED && !b->packed_ok) b->kernel = LMS_KERNEL_DIRECT;
     return LMS_OK;
 }
 
@@ -1822,6 +1881,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         (rc = A.get(&b->d_xy[2], N)) || (rc = A.get(&b->d_xy64, 2 * size_t(N))) || (rc = A.get(&b->d_fixed, 2 * size_t(N))) ||
         (rc = A.get(&b->d_cs, 4 * size_t(k))) ||
         (rc = A.get(&b->d_items, max_items)) || (rc = A.get(&b->d_item_mesh, max_items)) ||
+        (rc = A.get(&b->d_item_ebase, max_items)) ||
         (rc = ensure_queue(b, 64)) || (rc = orig.get(&d_rp0, N + 1)) || (rc = orig.get(&d_ci0, std::max(1, E))) ||
         (rc = orig.get(&d_inv, N)) || (rc = orig.get(&d_bnd0, N)))
         return fail_orig(rc);
@@ -1914,6 +1974,8 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     for (int r : status)
         if (r != LMS_OK) return fail_orig(r);
     // relabel on the device
+    int32_t max_deg_all = 0;
+    for (int32_t m = 0; m < k; ++m) max_deg_all = std::max(max_deg_all, max_row(meshes[m].row_ptr, meshes[m].n));
     std::vector<int32_t> inv(N);
     std::vector<int32_t>& rp = b->rp;
     rp.assign(N + 1, 0);
@@ -1924,6 +1986,10 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     if (!e) e = cudaMemcpyAsync(b->d_rp, rp.data(), 4 * size_t(N + 1), cudaMemcpyHostToDevice, s);
     if (!e) e = lms::launch_gather_rows(N, b->d_perm, d_rp0, d_ci0, b->d_rp, b->d_ci, d_inv, s);
     if (!e) e = lms::launch_boundary_bits(N, b->d_perm, d_bnd0, b->d_bits, s);
+    // rows farthest neighbour first (storage distance): a row's first chunk of gathers then holds the
+    // references most likely to miss L1, so their latency overlaps the rest of the row (FP32 Kahan sums, so
+    // the order moves results by rounding only; rows longer than kMaxPackedDegree keep their order)
+    if (!e && max_deg_all <= lms::kMaxPackedDegree) e = lms::launch_sort_rows_far_first(N, b->d_rp, b->d_ci, s);
     if (!e) e = lms::launch_flag_boundary_rows(N, b->d_bits, b->d_rp, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) {
@@ -1934,7 +2000,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     b->order_perm = b->perm;
     b->bnd_store.resize(N);
     for (int32_t i = 0; i < N; ++i) b->bnd_store[i] = bnd0[b->perm[i]];
-    if ((rc = batch_build_items(b, b->tile))) return fail(rc);
+    if ((rc = batch_build_items(b, b->tile)) || (rc = batch_build_row_words(b))) return fail(rc);
     e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_fixed, b->d_xy[0],
                                   b->d_xy[1], b->d_cs, b->d_err + 1, s);
     if (e) return fail(check_launch(e, "batch_load_xy"));
@@ -1968,6 +2034,13 @@ int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chu
         case LMS_KERNEL_SELL:
             if (chunk != 1 && chunk != 4 && chunk != 8) return LMS_ERR_ARG;
             break;
+        case LMS_KERNEL_PACKED:
+            if (chunk < 3 || chunk > 6) return LMS_ERR_ARG;
+            if (!b->packed_ok) {
+                lms::set_error_detail("packed rows need meshes of fewer than 2^22 CSR entries and rows of at most 63");
+                return LMS_ERR_ARG;
+            }
+            break;
         default:
             return LMS_ERR_ARG;
     }
@@ -1987,6 +2060,58 @@ int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chu
     return LMS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Chains of the sweep graph: times 10-sweep graphs of lms_batch_smooth with 1 to 4 chains on the current
+// launch configuration and keeps the fastest.  The batch's positions are saved in the scratch buffer
+// and put back, so the batch holds the same coordinates afterwards (the sweeps run an even count, so
+// the ping-pong index ends where it started; the other buffer's interior values are overwritten by the
+// next sweep before anything reads them).
+int batch_tune_chains(lms_batch_s* b) {
+    if (b->kernel == LMS_KERNEL_SELL || b->k < 2) return LMS_OK;
+    cudaStream_t s = b->stream;
+    const int cur = b->cur;
+    LMS_CUDA(cudaMemcpyAsync(b->d_xy[2], b->d_xy[cur], sizeof(float2) * size_t(b->n_total), cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t e0, e1;
+    LMS_CUDA(cudaEventCreate(&e0));
+    LMS_CUDA(cudaEventCreate(&e1));
+    const int iters = 10, reps = 3;
+    float best = 1e30f;
+    int win = b->chains;
+    const bool verbose = std::getenv("LMS_AUTOTUNE_VERBOSE") != nullptr;
+    int rc = LMS_OK;
+    for (int c = 1; c <= 4 && c <= b->k && rc == LMS_OK; ++c) {
+        b->chains = c;
+        if ((rc = lms_batch_smooth(b, iters)) != LMS_OK) break;  // capture + warm-up
+        float ms = 1e30f;
+        for (int round = 0; round < 2 && rc == LMS_OK; ++round) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) rc = LMS_ERR_CUDA;
+            for (int r = 0; r < reps && rc == LMS_OK; ++r) rc = lms_batch_smooth(b, iters);
+            if (rc == LMS_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                rc = LMS_ERR_CUDA;
+            float t = 0.f;
+            if (rc == LMS_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = std::min(ms, t);
+        }
+        if (verbose) std::fprintf(stderr, "[lms autotune] chains=%d: %.4f ms/sweep\n", c, ms / (reps * iters));
+        if (ms < best) {
+            best = ms;
+            win = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chains = win;
+    if (rc != LMS_OK) return rc;
+    LMS_CUDA(cudaMemcpyAsync(b->d_xy[cur], b->d_xy[2], sizeof(float2) * size_t(b->n_total), cudaMemcpyDeviceToDevice, s));
+    LMS_CUDA(cudaStreamSynchronize(s));
+    b->cur = cur;
+    return LMS_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* chunk, int32_t* tile,
                        int32_t* ctas_per_sm) {
     if (!b) return LMS_ERR_ARG;
@@ -1998,10 +2123,12 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string kk;
-            int kn, bl, ch, ti, cp, wi;
-            if ((is >> kk >> kn >> bl >> ch >> ti >> cp >> wi) && kk == key && batch_relayout(b, wi) == LMS_OK &&
-                lms_batch_set_config(b, kn, bl, ch, ti, cp) == LMS_OK)
+            int kn, bl, ch, ti, cp, wi, cn;
+            if ((is >> kk >> kn >> bl >> ch >> ti >> cp >> wi >> cn) && kk == key && cn >= 1 && cn <= 8 &&
+                batch_relayout(b, wi) == LMS_OK && lms_batch_set_config(b, kn, bl, ch, ti, cp) == LMS_OK) {
+                b->chains = cn;
                 return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
+            }
         }
     }
     struct Cand {
@@ -2018,6 +2145,10 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
     for (int ti : {512, 1024, 2048})  // sigma outermost: the SELL tables are rebuilt once per sigma
         for (int blk : {128, 256})
             for (int ch : {4, 8}) cands.push_back({LMS_KERNEL_SELL, blk, ch, ti, 0});
+    if (b->packed_ok)
+        for (int blk : {128, 256, 512})
+            for (int ch : {3, 4, 5, 6})
+                for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_PACKED, blk, ch, ti, 0});
     cudaStream_t s = b->stream;
     cudaEvent_t e0, e1;
     LMS_CUDA(cudaEventCreate(&e0));
@@ -2057,10 +2188,11 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
     cudaEventDestroy(e1);
     LMS_TRY(batch_relayout(b, win.window));
     LMS_TRY(lms_batch_set_config(b, win.kernel, win.block, win.chunk, win.tile, 0));
+    LMS_TRY(batch_tune_chains(b));
     if (cache) {
         std::ofstream f(cache, std::ios::app);
         f << key << " " << win.kernel << " " << win.block << " " << win.chunk << " " << win.tile << " 0 " << win.window
-          << "\n";
+          << " " << b->chains << "\n";
     }
     return lms_batch_get_config(b, kernel, block, chunk, tile, ctas_per_sm);
 }
@@ -2071,7 +2203,7 @@ int lms_batch_smooth(lms_batch b, int32_t iters) {
     if (!b->configured) LMS_TRY(lms_batch_autotune(b, nullptr, nullptr, nullptr, nullptr, nullptr));
     LMS_TRY(ensure_queue(b, iters));
     const int base = b->cur;
-    std::string key = std::to_string(iters) + "/" + std::to_string(base);
+    std::string key = std::to_string(iters) + "/" + std::to_string(base) + "/" + std::to_string(b->chains);
     cudaGraphExec_t exec;
     int64_t kernels = 0;
     auto it = b->graphs.execs.find(key);
@@ -2082,10 +2214,9 @@ int lms_batch_smooth(lms_batch b, int32_t iters) {
         const int grid = batch_grid(b);
         // The batch as parallel chains of sweeps in one graph, one per run of whole meshes with about
         // equal vertex counts: the meshes are independent, so the tail of one chain's sweep overlaps the
-        // other chain's work (two chains: 4% faster sweeps than one on the 512-mesh batch; three or more
-        // gain less).  SELL tiles are not ordered by mesh: one chain.
-        constexpr int kChains = 2;
-        const int chains = (b->kernel == LMS_KERNEL_SELL) ? 1 : std::max(1, std::min<int>(kChains, b->k));
+        // other chains' work (b->chains, picked by the autotuner; two chains gave 4% faster sweeps than one
+        // on the 512-mesh batch).  SELL tiles are not ordered by mesh: one chain.
+        const int chains = (b->kernel == LMS_KERNEL_SELL) ? 1 : std::max(1, std::min<int>(b->chains, b->k));
         std::vector<int32_t> cut(chains + 1, b->n_items);  // chain c: tiles [cut[c], cut[c+1])
         {
             const int tile = b->items_tile;
@@ -2320,6 +2451,18 @@ int lms_batch_info(lms_batch b, int64_t* n_total, int64_t* n_interior, int64_t* 
 int lms_batch_last_launches(lms_batch b, int64_t* launches) {
     if (!b || !launches) return LMS_ERR_ARG;
     *launches = b->last_launches;
+    return LMS_OK;
+}
+
+int lms_batch_set_chains(lms_batch b, int32_t chains) {
+    if (!b || chains < 1 || chains > 8) return LMS_ERR_ARG;
+    b->chains = chains;
+    return LMS_OK;
+}
+
+int lms_batch_get_chains(lms_batch b, int32_t* chains) {
+    if (!b || !chains) return LMS_ERR_ARG;
+    *chains = b->chains;
     return LMS_OK;
 }
 

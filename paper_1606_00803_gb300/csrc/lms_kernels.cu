@@ -382,6 +382,55 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
     }
 }
 
+// Batched FP32 Jacobi over packed row words: one 32-bit word per vertex holds its row's first entry
+// relative to its mesh's first entry (bits 0..21), its neighbour count (bits 22..27) and the boundary
+// flag (bit 31), so a thread learns its whole row from one coalesced load (no neighbour-lane shuffle, no
+// second load for the last lane).  Tiles come from the work queue as in k_batch_sweep; the mesh's first
+// entry comes with the tile (items_ebase).  Rows read CHUNK entries at a time - ids, then gathers, then
+// the Kahan sums in stored row order.
+template <int CHUNK>
+__global__ void __launch_bounds__(512) k_batch_sweep_packed(PackedArgs a) {
+    __shared__ int32_t s_item[2];
+    const float2* __restrict__ src = static_cast<const float2*>(a.src);
+    float2* __restrict__ dst = static_cast<float2*>(a.dst);
+    int buf = 0;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    for (;;) {
+        const int32_t item = s_item[buf];
+        if (item >= a.n_items) break;
+        if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
+        const int2 r = __ldg(a.items + item);
+        const int32_t ebase = __ldg(a.items_ebase + item);
+        for (int32_t v = r.x + static_cast<int32_t>(threadIdx.x); v < r.y; v += blockDim.x) {
+            const int32_t w = __ldg(a.row_words + v);
+            if (w < 0) continue;  // boundary vertex
+            const int32_t e0 = ebase + (w & kPackedOffsetMask), e1 = e0 + ((w >> kPackedDegreeShift) & kPackedDegreeMask);
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int32_t e = e0; e < e1; e += CHUNK) {
+                int32_t u[CHUNK];
+                float2 p[CHUNK];
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g) {
+                    u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
+                    if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+                }
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int g = 0; g < CHUNK; ++g)
+                    if (u[g] >= 0) {
+                        kahan_add(sx, cx, p[g].x);
+                        kahan_add(sy, cy, p[g].y);
+                    }
+            }
+            dst[v] = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
 // Batched FP32 Jacobi over a SELL-C-sigma work layout (Kreutzer et al., SIAM J. Sci. Comput. 36(5),
 // 2014): inside every tile the interior vertices are sorted by degree into slices of 32, and a slice's
 // neighbour ids are stored column-major (entry j of slot l at base + 32 j + l, -1 past the slot's row),
@@ -582,6 +631,24 @@ __global__ void k_stop_check(const double* __restrict__ partials, double n, DevS
     st->disp2[(k + 1) & 1] = 0ull;
 }
 
+// Each row's entries ordered by decreasing storage distance |u - v| (stable: equal distances keep their
+// order); one thread per row, insertion sort of at most kMaxPackedDegree entries in place.
+__global__ void k_sort_rows_far_first(int32_t n, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t e0 = row_ptr[v] & 0x7fffffff, e1 = row_ptr[v + 1] & 0x7fffffff;
+    for (int32_t i = e0 + 1; i < e1; ++i) {
+        const int32_t x = col_idx[i];
+        const int32_t dx = abs(x - v);
+        int32_t j = i - 1;
+        while (j >= e0 && abs(col_idx[j] - v) < dx) {
+            col_idx[j + 1] = col_idx[j];
+            --j;
+        }
+        col_idx[j + 1] = x;
+    }
+}
+
 __global__ void k_gather_rows(int32_t n, const int32_t* __restrict__ new_to_old, const int32_t* __restrict__ rp_src,
                               const int32_t* __restrict__ ci_src, const int32_t* __restrict__ rp_dst,
                               int32_t* __restrict__ ci_dst, const int32_t* __restrict__ map) {
@@ -777,6 +844,39 @@ int batch_sweep_occupancy(int block, int chunk) {
     int n = 0;
     if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
     return n;
+}
+
+using PackedKernel = void (*)(PackedArgs);
+
+PackedKernel packed_kernel(int chunk) {
+    switch (chunk) {
+        case 3: return k_batch_sweep_packed<3>;
+        case 4: return k_batch_sweep_packed<4>;
+        case 5: return k_batch_sweep_packed<5>;
+        case 6: return k_batch_sweep_packed<6>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_batch_sweep_packed(const PackedArgs& a, int block, int chunk, int grid, cudaStream_t stream) {
+    const PackedKernel k = packed_kernel(chunk);
+    if (k == nullptr) return cudaErrorInvalidValue;
+    if (a.n_items <= 0) return cudaSuccess;
+    k<<<grid, block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int batch_packed_occupancy(int block, int chunk) {
+    const PackedKernel k = packed_kernel(chunk);
+    int n = 0;
+    if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_sort_rows_far_first(int32_t n, const int32_t* row_ptr, int32_t* col_idx, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    k_sort_rows_far_first<<<blocks_for(n, 256), 256, 0, stream>>>(n, row_ptr, col_idx);
+    return cudaGetLastError();
 }
 
 using SellKernel = void (*)(SellArgs);

@@ -1,6 +1,7 @@
-"""The benchmark reports `roofline.traffic` from the committed ncu record only while the batched sweep
-kernel, its argument struct and the device helpers it calls are unchanged since the capture, and only
-for the launch configuration and chain count that were captured."""
+"""The benchmark reports `roofline.traffic` from the committed ncu record only while the recorded batched
+sweep kernel, its argument struct, the kernel that orders the batch's rows and the device helpers the
+sweep calls are unchanged since the capture, and only for the launch configuration and chain count that
+were captured."""
 import json
 import os
 import shutil
@@ -15,7 +16,7 @@ def record():
 
 def test_record_matches_the_sources_and_launch():
     t = record()
-    assert t["source_digest"] == bench.kernel_source_digest()
+    assert t["source_digest"] == bench.kernel_source_digest(t["kernel"])
     got = bench.load_traffic(t["kernel"], t["config"], t["launches_per_sweep"])
     assert got == t["dram_bytes_per_sweep"]
     # another launch configuration or chain count: no traffic figure
@@ -35,7 +36,7 @@ def copy_tree(tmp_path):
 
 def digest_of(root, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
-    return bench.kernel_source_digest()
+    return bench.kernel_source_digest(record()["kernel"])
 
 
 def edit(path, old, new):
@@ -53,9 +54,11 @@ def test_digest_follows_the_kernel_and_its_helpers_only(tmp_path, monkeypatch):
     edit(csrc / "lms_kernels.cu", "k_quality_partials_f64(int32_t ntri", "k_quality_partials_f64(int32_t  ntri")
     assert digest_of(root, monkeypatch) == base
     # the batched kernel's body, its argument struct, a helper it calls: each changes the digest
-    for path, old, new in ((csrc / "lms_kernels.cu", "if (v >= r.y || f0 < 0) continue;",
-                            "if (v >= r.y || f0 < 0) { continue; }"),
-                           (csrc / "lms_internal.h", "int32_t n_items;", "int32_t n_items;  // tiles"),
+    for path, old, new in ((csrc / "lms_kernels.cu", "if (w < 0) continue;  // boundary vertex",
+                            "if (w < 0) { continue; }  // boundary vertex"),
+                           (csrc / "lms_internal.h", "const int32_t* items_ebase;", "const int32_t*  items_ebase;"),
+                           (csrc / "lms_kernels.cu", "while (j >= e0 && abs(col_idx[j] - v) < dx) {",
+                            "while (j >= e0 && abs(col_idx[j] - v) < dx)  {"),
                            (csrc / "lms_device.cuh", "c = __fsub_rn(__fsub_rn(t, s), y);",
                             "c = __fsub_rn(__fsub_rn(t, s), y);  // compensation")):
         saved = path.read_text()

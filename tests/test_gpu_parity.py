@@ -297,7 +297,9 @@ def small_batch(count=10):
                                     (lms.KERNEL_DIRECT, 256, 5, 256), (lms.KERNEL_DIRECT, 128, 6, 512),
                                     (lms.KERNEL_SELL, 128, 1, 256),
                                     (lms.KERNEL_SELL, 256, 4, 1024), (lms.KERNEL_SELL, 512, 8, 2048),
-                                    (lms.KERNEL_SELL, 128, 4, 128)])
+                                    (lms.KERNEL_SELL, 128, 4, 128),
+                                    (lms.KERNEL_PACKED, 128, 5, 512), (lms.KERNEL_PACKED, 256, 3, 256),
+                                    (lms.KERNEL_PACKED, 512, 6, 1024), (lms.KERNEL_PACKED, 128, 4, 128)])
 def test_batched_fp32_matches_oracle(config):
     meshes = small_batch()
     with lms.Batch(meshes, ordering=lms.RDR) as b:
@@ -328,7 +330,7 @@ def test_batched_autotune_keeps_positions():
     with lms.Batch(meshes, ordering=lms.BFS) as b:
         before = b.all_coords()
         cfg = b.autotune()
-        assert cfg["kernel"] in (lms.KERNEL_DIRECT, lms.KERNEL_STAGED, lms.KERNEL_SELL)
+        assert cfg["kernel"] in (lms.KERNEL_DIRECT, lms.KERNEL_STAGED, lms.KERNEL_SELL, lms.KERNEL_PACKED)
         assert cfg["block"] in (128, 256, 512) and cfg["chunk"] in (1, 2, 3, 4, 5, 6, 8)
         assert np.array_equal(b.all_coords(), before)
         b.smooth(7)
@@ -339,11 +341,75 @@ def test_batched_autotune_keeps_positions():
         assert err(got[sum(len(x["xy"]) for x in meshes[:i]):][: m["n"]], want, m) <= TOL32
 
 
+def test_batched_kernels_agree_bit_for_bit():
+    """Every batched kernel reads the same rows in the same entry order and sums them the same way, so the
+    FP32 results of the direct, packed, staged and SELL kernels are identical."""
+    meshes = small_batch()
+    with lms.Batch(meshes, ordering=lms.RDR) as b:
+        xy = np.concatenate([m["xy"] for m in meshes])
+        ref = None
+        for cfg in ((lms.KERNEL_DIRECT, 128, 5, 512), (lms.KERNEL_PACKED, 128, 5, 512),
+                    (lms.KERNEL_PACKED, 256, 6, 256), (lms.KERNEL_STAGED, 128, 1, 256), (lms.KERNEL_SELL, 128, 4, 512)):
+            b.set_config(*cfg)
+            b.set_all_coords(xy)
+            b.smooth(17)
+            got = b.all_coords()
+            if ref is None:
+                ref = got
+            assert np.array_equal(got, ref), cfg
+
+
+def test_sweep_chains_do_not_change_results():
+    """lms_batch_set_chains only changes how the sweeps of the meshes are grouped into parallel launch chains."""
+    meshes = small_batch()
+    xy = np.concatenate([m["xy"] for m in meshes])
+    with lms.Batch(meshes, ordering=lms.RDR) as b:
+        b.set_config(lms.KERNEL_PACKED, 128, 5, 256)
+        ref = None
+        for c in (1, 2, 3, 4, 8):
+            b.set_chains(c)
+            assert b.chains() == c
+            b.set_all_coords(xy)
+            b.smooth(13)
+            got = b.all_coords()
+            if ref is None:
+                ref = got
+            assert np.array_equal(got, ref), c
+        for bad in (0, 9, -1):
+            with pytest.raises(lms.LmsError):
+                b.set_chains(bad)
+        before = b.all_coords()
+        cfg = b.autotune()
+        assert 1 <= cfg["chains"] <= 4
+        assert np.array_equal(b.all_coords(), before)  # the chain timing leaves the coordinates in place
+
+
+def test_packed_kernel_unavailable_for_a_mesh_of_2_22_entries():
+    """The packed row word holds a row's offset within its mesh in 22 bits: a batch holding a mesh of 2^22
+    CSR entries or more refuses the packed kernel, and the autotuner never picks it; the other kernels
+    still run and match the oracle."""
+    big = meshgen.generate(850, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=77)
+    assert big["nnz"] >= 2 ** 22
+    meshes = [big] + small_batch(3)
+    with lms.Batch(meshes, ordering=lms.BFS) as b:
+        with pytest.raises(lms.LmsError):
+            b.set_config(lms.KERNEL_PACKED, 128, 5, 512)
+        b.set_config(lms.KERNEL_DIRECT, 128, 5, 512)
+        b.smooth(5)
+        for i, m in enumerate(meshes):
+            want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 5)
+            assert err(b.coords(i), want, m) <= TOL32
+        assert b.autotune()["kernel"] != lms.KERNEL_PACKED
+
+
 def test_batched_config_rejects_unsupported_chunks():
     with lms.Batch(small_batch(2), ordering=lms.ORI) as b:
         for chunk in (0, 7, 9, -1):
             with pytest.raises(lms.LmsError):
                 b.set_config(lms.KERNEL_DIRECT, 128, chunk, 512)
+        for chunk in (1, 2, 7, 8):
+            with pytest.raises(lms.LmsError):
+                b.set_config(lms.KERNEL_PACKED, 128, chunk, 512)
         with pytest.raises(lms.LmsError):
             b.set_config(lms.KERNEL_SELL, 128, 3, 512)
 
