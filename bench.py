@@ -803,7 +803,7 @@ def run_ours(args, dist):
 def kernel_name(cfg):
     import paper_1606_00803_gb300 as lms
     return {lms.KERNEL_STAGED: "k_sweep_staged<fp32>", lms.KERNEL_SELL: "k_batch_sell<%d>" % cfg["chunk"],
-            lms.KERNEL_PACKED: "k_batch_sweep_packed<%d>" % cfg["chunk"]}.get(cfg["kernel"],
+            lms.KERNEL_PACKED: "k_batch_sweep_packed<%d>" % (cfg["chunk"] // 2)}.get(cfg["kernel"],
                                                                               "k_batch_sweep<%d>" % cfg["chunk"])
 
 
@@ -830,7 +830,7 @@ def kernel_source_digest(kernel="k_batch_sweep"):
     device = open(os.path.join(csrc, "lms_device.cuh")).read()
     checks = device.index("#ifdef LMS_CHECKS")
     if kernel.startswith("k_batch_sweep_packed"):
-        body = _braced_block(kernels, kernels.index("template <int CHUNK>\n__global__ void __launch_bounds__(512) "
+        body = _braced_block(kernels, kernels.index("template <int PAIRS>\n__global__ void __launch_bounds__(512) "
                                                     "k_batch_sweep_packed"))
         args = internal[internal.index("constexpr int kPackedDegreeShift"):internal.index("cudaError_t launch_batch_sweep_packed")]
     else:

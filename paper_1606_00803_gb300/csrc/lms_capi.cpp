@@ -1347,9 +1347,12 @@ struct lms_batch_s {
     uint32_t* d_bits = nullptr;
     int2* d_items = nullptr;
     int4* d_items4 = nullptr;           // (first vertex, end vertex, first entry, end entry)
-    int32_t* d_item_ebase = nullptr;    // per tile: first CSR entry of the tile's mesh (packed kernel)
-    int32_t* d_rw = nullptr;            // packed row words (LMS_KERNEL_PACKED), null when the batch does not fit
-    bool packed_ok = false;             // every mesh < 2^22 entries and every row <= kMaxPackedDegree entries
+    int32_t* d_item_pbase = nullptr;    // per tile: first id pair of the tile's mesh (packed kernel)
+    int32_t* d_rw = nullptr;            // packed row words (LMS_KERNEL_PACKED)
+    int2* d_pairs = nullptr;            // rows padded to even length, read as id pairs (LMS_KERNEL_PACKED)
+    int64_t pairs_cap = 0;
+    std::vector<int32_t> pstart;        // first id pair of each storage position's row (host copy)
+    bool packed_ok = false;             // every mesh < 2^22 id pairs and every row <= kMaxPackedDegree entries
     int32_t e_cap = 0;                  // max CSR entries of a tile
     // SELL-C-sigma work layout (built on demand for the current tile size)
     int32_t* d_sell_col = nullptr;
@@ -1423,10 +1426,10 @@ int batch_build_items(lms_batch_s* b, int tile) {
             items4.push_back(make_int4(va, vb, b->rp[va], b->rp[vb]));
             e_cap = std::max(e_cap, b->rp[vb] - b->rp[va]);
             im.push_back(m);
-            ieb.push_back(b->rp[b->voff[m]]);
+            ieb.push_back(b->pstart.empty() ? 0 : b->pstart[b->voff[m]]);
         }
     if (int64_t(items.size()) > b->items_capacity) return LMS_ERR_STATE;
-    LMS_CUDA(cudaMemcpyAsync(b->d_item_ebase, ieb.data(), sizeof(int32_t) * ieb.size(), cudaMemcpyHostToDevice,
+    LMS_CUDA(cudaMemcpyAsync(b->d_item_pbase, ieb.data(), sizeof(int32_t) * ieb.size(), cudaMemcpyHostToDevice,
                              b->stream));
     LMS_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream));
     LMS_CUDA(cudaMemcpyAsync(b->d_items4, items4.data(), sizeof(int4) * items4.size(), cudaMemcpyHostToDevice,
@@ -1511,26 +1514,51 @@ int batch_build_sell(lms_batch_s* b, int sigma) {
     return LMS_OK;
 }
 
-// Packed row words of the current layout (LMS_KERNEL_PACKED): offset of the row within its mesh's entries,
-// neighbour count, boundary flag.  Leaves packed_ok false (and the kernel unavailable) when a mesh has
-// 2^22 entries or more or a row more than kMaxPackedDegree entries.
+// Packed rows of the current layout (LMS_KERNEL_PACKED): every interior row copied into the id-pair array
+// padded to an even length, and per vertex one word with the row's first pair relative to its mesh's,
+// its neighbour count and the boundary flag.  Leaves packed_ok false (and the kernel unavailable) when a
+// mesh has 2^22 id pairs or more or a row more than kMaxPackedDegree entries.  The tile table's per-tile
+// mesh pair bases come from pstart: rebuild the tile table after this.
 int batch_build_row_words(lms_batch_s* b) {
     b->packed_ok = false;
+    b->pstart.clear();
     const int32_t N = int32_t(b->n_total);
-    std::vector<int32_t> rw(N);
+    std::vector<int32_t> ps(size_t(N) + 1, 0), rw(N);
+    for (int32_t v = 0; v < N; ++v) {
+        const int32_t d = b->rp[v + 1] - b->rp[v];
+        if (d > lms::kMaxPackedDegree) return LMS_OK;
+        ps[v + 1] = ps[v] + (b->bnd_store[v] ? 0 : (d + 1) / 2);
+    }
     for (int32_t m = 0; m < b->k; ++m) {
         const int32_t v0 = int32_t(b->voff[m]), v1 = int32_t(b->voff[m + 1]);
-        if (int64_t(b->rp[v1]) - b->rp[v0] > lms::kPackedOffsetMask) return LMS_OK;
-        for (int32_t v = v0; v < v1; ++v) {
-            const int32_t d = b->rp[v + 1] - b->rp[v];
-            if (d > lms::kMaxPackedDegree) return LMS_OK;
-            rw[v] = (b->rp[v] - b->rp[v0]) | (d << lms::kPackedDegreeShift) |
+        if (ps[v1] - ps[v0] > lms::kPackedOffsetMask) return LMS_OK;
+        for (int32_t v = v0; v < v1; ++v)
+            rw[v] = (ps[v] - ps[v0]) | ((b->rp[v + 1] - b->rp[v]) << lms::kPackedDegreeShift) |
                     (b->bnd_store[v] ? int32_t(0x80000000u) : 0);
-        }
     }
+    const int64_t P = ps[N];
     if (!b->d_rw) LMS_TRY(b->arena.get(&b->d_rw, std::max(1, N)));
-    LMS_CUDA(cudaMemcpyAsync(b->d_rw, rw.data(), sizeof(int32_t) * size_t(N), cudaMemcpyHostToDevice, b->stream));
-    LMS_CUDA(cudaStreamSynchronize(b->stream));
+    if (P + 1 > b->pairs_cap) {
+        // sized for the largest padding any layout of these rows can need: one pair per vertex beyond E / 2
+        const int64_t cap = std::max<int64_t>(P + 1, (b->nnz_total + b->n_total) / 2 + 1);
+        LMS_TRY(b->arena.get(&b->d_pairs, size_t(cap)));
+        b->pairs_cap = cap;
+    }
+    Arena tmp;
+    tmp.al = b->arena.al;
+    tmp.stream = b->stream;
+    int32_t* d_ps = nullptr;
+    if (int rc = tmp.get(&d_ps, size_t(N) + 1)) return rc;
+    cudaError_t e = cudaMemcpyAsync(d_ps, ps.data(), sizeof(int32_t) * (size_t(N) + 1), cudaMemcpyHostToDevice, b->stream);
+    if (!e) e = cudaMemcpyAsync(b->d_rw, rw.data(), sizeof(int32_t) * size_t(N), cudaMemcpyHostToDevice, b->stream);
+    if (!e) e = lms::launch_pad_rows(N, b->d_rp, b->d_ci, d_ps, reinterpret_cast<int32_t*>(b->d_pairs), b->stream);
+    if (!e) e = cudaStreamSynchronize(b->stream);
+    tmp.release_all();
+    if (e) {
+        lms::set_error_detail(std::string("packed rows: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    b->pstart.swap(ps);
     b->packed_ok = true;
     return LMS_OK;
 }
@@ -1538,11 +1566,11 @@ int batch_build_row_words(lms_batch_s* b) {
 lms::PackedArgs batch_packed_args(lms_batch_s* b, int src, int dst, int slot) {
     lms::PackedArgs a{};
     a.row_words = b->d_rw;
-    a.col_idx = b->d_ci;
+    a.id_pairs = b->d_pairs;
     a.src = b->d_xy[src];
     a.dst = b->d_xy[dst];
     a.items = b->d_items;
-    a.items_ebase = b->d_item_ebase;
+    a.items_pbase = b->d_item_pbase;
     a.n_items = b->n_items;
     a.queue = b->d_queue + slot;
     a.n_vertices = int32_t(b->n_total);
@@ -1602,7 +1630,7 @@ int batch_issue_range(lms_batch_s* b, int src, int dst, int slot, int grid, cuda
     if (b->kernel == LMS_KERNEL_PACKED) {
         lms::PackedArgs a = batch_packed_args(b, src, dst, slot);
         a.items += i0;
-        a.items_ebase += i0;
+        a.items_pbase += i0;
         a.n_items = i1 - i0;
         return check_launch(lms::launch_batch_sweep_packed(a, b->block, b->chunk, grid, s), "batch_sweep_packed");
     }
@@ -1667,7 +1695,7 @@ std::string autotune_key(lms_batch_s* b) {
         return l;
     };
     std::ostringstream os;
-    os << "v11|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
+    os << "v12|" << p.name << "|fp32|jacobi|n2^" << bucket(b->n_total) << "|nnz2^" << bucket(b->nnz_total);
     std::string s = os.str();
     for (auto& c : s)
         if (c == ' ') c = '_';
@@ -1767,8 +1795,8 @@ int batch_relayout(lms_batch_s* b, int32_t window) {
     b->graphs.clear();
     b->items_tile = 0;
     b->sell_sigma = 0;
-    LMS_TRY(batch_build_items(b, b->tile));
     LMS_TRY(batch_build_row_words(b));
+    LMS_TRY(batch_build_items(b, b->tile));
     if (b->kernel == LMS_KERNEL_SELL) LMS_TRY(batch_build_sell(b, b->tile));
     if (b->kernel == LMS_KERNEL_PACKED && !b->packed_ok) b->kernel = LMS_KERNEL_DIRECT;
     return LMS_OK;
@@ -1881,7 +1909,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
         (rc = A.get(&b->d_xy[2], N)) || (rc = A.get(&b->d_xy64, 2 * size_t(N))) || (rc = A.get(&b->d_fixed, 2 * size_t(N))) ||
         (rc = A.get(&b->d_cs, 4 * size_t(k))) ||
         (rc = A.get(&b->d_items, max_items)) || (rc = A.get(&b->d_item_mesh, max_items)) ||
-        (rc = A.get(&b->d_item_ebase, max_items)) ||
+        (rc = A.get(&b->d_item_pbase, max_items)) ||
         (rc = ensure_queue(b, 64)) || (rc = orig.get(&d_rp0, N + 1)) || (rc = orig.get(&d_ci0, std::max(1, E))) ||
         (rc = orig.get(&d_inv, N)) || (rc = orig.get(&d_bnd0, N)))
         return fail_orig(rc);
@@ -2000,7 +2028,7 @@ int lms_batch_create(int32_t k, const lms_mesh_desc* meshes, int ordering, uint6
     b->order_perm = b->perm;
     b->bnd_store.resize(N);
     for (int32_t i = 0; i < N; ++i) b->bnd_store[i] = bnd0[b->perm[i]];
-    if ((rc = batch_build_items(b, b->tile)) || (rc = batch_build_row_words(b))) return fail(rc);
+    if ((rc = batch_build_row_words(b)) || (rc = batch_build_items(b, b->tile))) return fail(rc);
     e = lms::launch_batch_load_xy(b->n_items, b->d_items, b->d_item_mesh, b->d_perm, b->d_fixed, b->d_xy[0],
                                   b->d_xy[1], b->d_cs, b->d_err + 1, s);
     if (e) return fail(check_launch(e, "batch_load_xy"));
@@ -2035,9 +2063,9 @@ int lms_batch_set_config(lms_batch b, int32_t kernel, int32_t block, int32_t chu
             if (chunk != 1 && chunk != 4 && chunk != 8) return LMS_ERR_ARG;
             break;
         case LMS_KERNEL_PACKED:
-            if (chunk < 3 || chunk > 6) return LMS_ERR_ARG;
+            if (chunk != 2 && chunk != 4 && chunk != 6) return LMS_ERR_ARG;
             if (!b->packed_ok) {
-                lms::set_error_detail("packed rows need meshes of fewer than 2^22 CSR entries and rows of at most 63");
+                lms::set_error_detail("packed rows need meshes of fewer than 2^22 id pairs and rows of at most 63");
                 return LMS_ERR_ARG;
             }
             break;
@@ -2147,7 +2175,7 @@ int lms_batch_autotune(lms_batch b, int32_t* kernel, int32_t* block, int32_t* ch
             for (int ch : {4, 8}) cands.push_back({LMS_KERNEL_SELL, blk, ch, ti, 0});
     if (b->packed_ok)
         for (int blk : {128, 256, 512})
-            for (int ch : {3, 4, 5, 6})
+            for (int ch : {2, 4, 6})
                 for (int ti : {256, 512, 1024}) cands.push_back({LMS_KERNEL_PACKED, blk, ch, ti, 0});
     cudaStream_t s = b->stream;
     cudaEvent_t e0, e1;

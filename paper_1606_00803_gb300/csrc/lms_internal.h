@@ -196,26 +196,31 @@ struct SellArgs {
 cudaError_t launch_batch_sell(const SellArgs& a, int block, int chunk, int grid, cudaStream_t stream);
 int batch_sell_occupancy(int block, int chunk);
 
-// Batched FP32 sweep over packed row words (k_batch_sweep_packed): row_words[v] = (first entry of v's row -
-// first entry of v's mesh) | neighbour count << kPackedDegreeShift | boundary << 31.  A batch can use it
-// when every mesh has fewer than 2^22 CSR entries and every row at most kMaxPackedDegree entries.
+// Batched FP32 sweep over packed rows (k_batch_sweep_packed): row_words[v] = (first id pair of v's row -
+// first id pair of v's mesh) | neighbour count << kPackedDegreeShift | boundary << 31; id_pairs holds every
+// row padded to an even length with -1.  A batch can use it when every mesh has fewer than 2^22 id pairs
+// and every row at most kMaxPackedDegree entries.
 constexpr int kPackedDegreeShift = 22;
 constexpr int32_t kPackedOffsetMask = (1 << kPackedDegreeShift) - 1;
 constexpr int32_t kPackedDegreeMask = 63;
 constexpr int kMaxPackedDegree = 63;
 struct PackedArgs {
     const int32_t* row_words;
-    const int32_t* col_idx;
+    const int2* id_pairs;
     const void* src;               // float2 positions read
     void* dst;                     // float2 positions written
     const int2* items;             // work-queue tiles (first vertex, end vertex)
-    const int32_t* items_ebase;    // per tile: first CSR entry of the tile's mesh
+    const int32_t* items_pbase;    // per tile: first id pair of the tile's mesh
     int32_t n_items;
     int32_t* queue;                // work-queue counter for this sweep
-    int32_t n_vertices;            // vertices addressable by col_idx (bounds checks of debug builds)
+    int32_t n_vertices;            // vertices addressable by the ids (bounds checks of debug builds)
 };
+// chunk = ids per step: 2, 4 or 6
 cudaError_t launch_batch_sweep_packed(const PackedArgs& a, int block, int chunk, int grid, cudaStream_t stream);
-int batch_packed_occupancy(int block, int chunk);  // chunk 3 to 6; resident CTAs per SM (0 on error)
+int batch_packed_occupancy(int block, int chunk);  // resident CTAs per SM (0 on error)
+// out[2 pstart[v] ...] = row v of (row_ptr, col_idx) padded with -1 to 2 (pstart[v + 1] - pstart[v]) ids
+cudaError_t launch_pad_rows(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* pstart,
+                            int32_t* out, cudaStream_t stream);
 // Orders every row's entries by decreasing |u - v| (stable); rows of at most kMaxPackedDegree entries.
 // row_ptr may carry the boundary flag in bit 31.
 cudaError_t launch_sort_rows_far_first(int32_t n, const int32_t* row_ptr, int32_t* col_idx, cudaStream_t stream);

@@ -382,13 +382,13 @@ __global__ void __launch_bounds__(512) k_batch_sweep(SweepArgs a) {
     }
 }
 
-// Batched FP32 Jacobi over packed row words: one 32-bit word per vertex holds its row's first entry
-// relative to its mesh's first entry (bits 0..21), its neighbour count (bits 22..27) and the boundary
-// flag (bit 31), so a thread learns its whole row from one coalesced load (no neighbour-lane shuffle, no
-// second load for the last lane).  Tiles come from the work queue as in k_batch_sweep; the mesh's first
-// entry comes with the tile (items_ebase).  Rows read CHUNK entries at a time - ids, then gathers, then
-// the Kahan sums in stored row order.
-template <int CHUNK>
+// Batched FP32 Jacobi over packed rows: one 32-bit word per vertex holds its row's first id pair relative
+// to its mesh's first pair (bits 0..21), its neighbour count (bits 22..27) and the boundary flag (bit 31),
+// so a thread learns its whole row from one coalesced load (no neighbour-lane shuffle, no second load for
+// the last lane), issued one round of the tile ahead.  Every row of the id array is padded to an even length with -1, so ids are read as
+// aligned pairs: PAIRS 8-byte loads per step, then the gathers, then the Kahan sums in stored row order.
+// Tiles come from the work queue as in k_batch_sweep; the mesh's first pair comes with the tile.
+template <int PAIRS>
 __global__ void __launch_bounds__(512) k_batch_sweep_packed(PackedArgs a) {
     __shared__ int32_t s_item[2];
     const float2* __restrict__ src = static_cast<const float2*>(a.src);
@@ -401,30 +401,41 @@ __global__ void __launch_bounds__(512) k_batch_sweep_packed(PackedArgs a) {
         if (item >= a.n_items) break;
         if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
         const int2 r = __ldg(a.items + item);
-        const int32_t ebase = __ldg(a.items_ebase + item);
-        for (int32_t v = r.x + static_cast<int32_t>(threadIdx.x); v < r.y; v += blockDim.x) {
-            const int32_t w = __ldg(a.row_words + v);
+        const int32_t pbase = __ldg(a.items_pbase + item);
+        // the row word of the thread's next vertex is loaded one round ahead, so a round starts with its
+        // id loads instead of waiting for its row word
+        int32_t vn = r.x + static_cast<int32_t>(threadIdx.x);
+        int32_t wn = vn < r.y ? __ldg(a.row_words + vn) : -1;
+        for (int32_t v = vn; v < r.y; v += blockDim.x) {
+            const int32_t w = wn;
+            vn = v + static_cast<int32_t>(blockDim.x);
+            wn = vn < r.y ? __ldg(a.row_words + vn) : -1;
             if (w < 0) continue;  // boundary vertex
-            const int32_t e0 = ebase + (w & kPackedOffsetMask), e1 = e0 + ((w >> kPackedDegreeShift) & kPackedDegreeMask);
+            const int32_t d = (w >> kPackedDegreeShift) & kPackedDegreeMask;
+            const int32_t q0 = pbase + (w & kPackedOffsetMask), q1 = q0 + ((d + 1) >> 1);
             float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-            for (int32_t e = e0; e < e1; e += CHUNK) {
-                int32_t u[CHUNK];
-                float2 p[CHUNK];
+            for (int32_t q = q0; q < q1; q += PAIRS) {
+                int32_t u[2 * PAIRS];
+                float2 p[2 * PAIRS];
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g) {
-                    u[g] = e + g < e1 ? __ldg(a.col_idx + e + g) : -1;
-                    if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+                for (int g = 0; g < PAIRS; ++g) {
+                    const int2 x = q + g < q1 ? __ldg(a.id_pairs + q + g) : make_int2(-1, -1);
+                    u[2 * g] = x.x;
+                    u[2 * g + 1] = x.y;
                 }
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+                for (int g = 0; g < 2 * PAIRS; ++g)
+                    if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
 #pragma unroll
-                for (int g = 0; g < CHUNK; ++g)
+                for (int g = 0; g < 2 * PAIRS; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int g = 0; g < 2 * PAIRS; ++g)
                     if (u[g] >= 0) {
                         kahan_add(sx, cx, p[g].x);
                         kahan_add(sy, cy, p[g].y);
                     }
             }
-            dst[v] = make_float2(mean_f32(sx, cx, e1 - e0), mean_f32(sy, cy, e1 - e0));
+            dst[v] = make_float2(mean_f32(sx, cx, d), mean_f32(sy, cy, d));
         }
         __syncthreads();
         buf ^= 1;
@@ -848,12 +859,12 @@ int batch_sweep_occupancy(int block, int chunk) {
 
 using PackedKernel = void (*)(PackedArgs);
 
+// chunk = ids read per step (pairs of ids: 2, 4 or 6)
 PackedKernel packed_kernel(int chunk) {
     switch (chunk) {
-        case 3: return k_batch_sweep_packed<3>;
-        case 4: return k_batch_sweep_packed<4>;
-        case 5: return k_batch_sweep_packed<5>;
-        case 6: return k_batch_sweep_packed<6>;
+        case 2: return k_batch_sweep_packed<1>;
+        case 4: return k_batch_sweep_packed<2>;
+        case 6: return k_batch_sweep_packed<3>;
         default: return nullptr;
     }
 }
@@ -871,6 +882,23 @@ int batch_packed_occupancy(int block, int chunk) {
     int n = 0;
     if (k == nullptr || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0) != cudaSuccess) return 0;
     return n;
+}
+
+// Row v of the CSR copied to id pairs [pstart[v], pstart[v + 1]) (in ids: 2 * pstart), -1 past its end.
+__global__ void k_pad_rows(int32_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                           const int32_t* __restrict__ pstart, int32_t* __restrict__ out) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t e0 = row_ptr[v] & 0x7fffffff, e1 = row_ptr[v + 1] & 0x7fffffff;
+    const int64_t o0 = 2 * static_cast<int64_t>(pstart[v]), o1 = 2 * static_cast<int64_t>(pstart[v + 1]);
+    for (int64_t k = o0; k < o1; ++k) out[k] = e0 + (k - o0) < e1 ? col_idx[e0 + (k - o0)] : -1;
+}
+
+cudaError_t launch_pad_rows(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* pstart,
+                            int32_t* out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    k_pad_rows<<<blocks_for(n, 256), 256, 0, stream>>>(n, row_ptr, col_idx, pstart, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sort_rows_far_first(int32_t n, const int32_t* row_ptr, int32_t* col_idx, cudaStream_t stream) {

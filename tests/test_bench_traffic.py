@@ -56,7 +56,7 @@ def test_digest_follows_the_kernel_and_its_helpers_only(tmp_path, monkeypatch):
     # the batched kernel's body, its argument struct, a helper it calls: each changes the digest
     for path, old, new in ((csrc / "lms_kernels.cu", "if (w < 0) continue;  // boundary vertex",
                             "if (w < 0) { continue; }  // boundary vertex"),
-                           (csrc / "lms_internal.h", "const int32_t* items_ebase;", "const int32_t*  items_ebase;"),
+                           (csrc / "lms_internal.h", "const int32_t* items_pbase;", "const int32_t*  items_pbase;"),
                            (csrc / "lms_kernels.cu", "while (j >= e0 && abs(col_idx[j] - v) < dx) {",
                             "while (j >= e0 && abs(col_idx[j] - v) < dx)  {"),
                            (csrc / "lms_device.cuh", "c = __fsub_rn(__fsub_rn(t, s), y);",

@@ -66,7 +66,7 @@ xy = np.concatenate([mm["xy"] for mm in meshes])
 wants = [oracle.smooth(mm["row_ptr"], mm["col_idx"], mm["is_boundary"], mm["xy"], 11)[0] for mm in meshes]
 for o in (lms.RDR, lms.BFS, lms.BRDR):
     for cfg in ((lms.KERNEL_DIRECT, 128, 4, 256), (lms.KERNEL_STAGED, 128, 1, 256), (lms.KERNEL_SELL, 128, 4, 256),
-                (lms.KERNEL_PACKED, 128, 5, 256)):
+                (lms.KERNEL_PACKED, 128, 4, 256)):
         with lms.Batch(meshes, ordering=o) as b:
             b.set_config(*cfg)
             got = b.run(xy, 11, groups=1 if cfg[0] == lms.KERNEL_SELL else 2)

@@ -37,7 +37,7 @@ def test_layout_windows_bit_identical_and_match_oracle(ordering):
             b.set_layout(window)
             assert b.layout() == window
             for cfg in ((lms.KERNEL_DIRECT, 128, 5, 512), (lms.KERNEL_DIRECT, 256, 6, 1024),
-                        (lms.KERNEL_PACKED, 128, 5, 512),
+                        (lms.KERNEL_PACKED, 128, 4, 512),
                         (lms.KERNEL_SELL, 128, 4, 256), (lms.KERNEL_STAGED, 128, 1, 256)):
                 b.set_config(*cfg)
                 b.set_all_coords(np.concatenate([m["xy"] for m in meshes]))

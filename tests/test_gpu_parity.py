@@ -298,7 +298,7 @@ def small_batch(count=10):
                                     (lms.KERNEL_SELL, 128, 1, 256),
                                     (lms.KERNEL_SELL, 256, 4, 1024), (lms.KERNEL_SELL, 512, 8, 2048),
                                     (lms.KERNEL_SELL, 128, 4, 128),
-                                    (lms.KERNEL_PACKED, 128, 5, 512), (lms.KERNEL_PACKED, 256, 3, 256),
+                                    (lms.KERNEL_PACKED, 128, 4, 512), (lms.KERNEL_PACKED, 256, 2, 256),
                                     (lms.KERNEL_PACKED, 512, 6, 1024), (lms.KERNEL_PACKED, 128, 4, 128)])
 def test_batched_fp32_matches_oracle(config):
     meshes = small_batch()
@@ -348,8 +348,9 @@ def test_batched_kernels_agree_bit_for_bit():
     with lms.Batch(meshes, ordering=lms.RDR) as b:
         xy = np.concatenate([m["xy"] for m in meshes])
         ref = None
-        for cfg in ((lms.KERNEL_DIRECT, 128, 5, 512), (lms.KERNEL_PACKED, 128, 5, 512),
-                    (lms.KERNEL_PACKED, 256, 6, 256), (lms.KERNEL_STAGED, 128, 1, 256), (lms.KERNEL_SELL, 128, 4, 512)):
+        for cfg in ((lms.KERNEL_DIRECT, 128, 5, 512), (lms.KERNEL_PACKED, 128, 4, 512),
+                    (lms.KERNEL_PACKED, 256, 6, 256), (lms.KERNEL_PACKED, 512, 2, 1024), (lms.KERNEL_STAGED, 128, 1, 256),
+                    (lms.KERNEL_SELL, 128, 4, 512)):
             b.set_config(*cfg)
             b.set_all_coords(xy)
             b.smooth(17)
@@ -364,7 +365,7 @@ def test_sweep_chains_do_not_change_results():
     meshes = small_batch()
     xy = np.concatenate([m["xy"] for m in meshes])
     with lms.Batch(meshes, ordering=lms.RDR) as b:
-        b.set_config(lms.KERNEL_PACKED, 128, 5, 256)
+        b.set_config(lms.KERNEL_PACKED, 128, 4, 256)
         ref = None
         for c in (1, 2, 3, 4, 8):
             b.set_chains(c)
@@ -384,16 +385,17 @@ def test_sweep_chains_do_not_change_results():
         assert np.array_equal(b.all_coords(), before)  # the chain timing leaves the coordinates in place
 
 
-def test_packed_kernel_unavailable_for_a_mesh_of_2_22_entries():
-    """The packed row word holds a row's offset within its mesh in 22 bits: a batch holding a mesh of 2^22
-    CSR entries or more refuses the packed kernel, and the autotuner never picks it; the other kernels
-    still run and match the oracle."""
-    big = meshgen.generate(850, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=77)
-    assert big["nnz"] >= 2 ** 22
+def test_packed_kernel_unavailable_for_a_mesh_of_2_22_id_pairs():
+    """The packed row word holds a row's offset within its mesh in 22 bits (in id pairs): a batch holding a
+    mesh of 2^22 id pairs or more refuses the packed kernel, and the autotuner never picks it; the other
+    kernels still run and match the oracle."""
+    big = meshgen.generate(1200, jitter=0.3, flip_frac=0.10, split_frac=0.05, seed=77)
+    deg = np.diff(big["row_ptr"])
+    assert int(((deg + 1) // 2)[big["is_boundary"] == 0].sum()) >= 2 ** 22  # id pairs of its interior rows
     meshes = [big] + small_batch(3)
     with lms.Batch(meshes, ordering=lms.BFS) as b:
         with pytest.raises(lms.LmsError):
-            b.set_config(lms.KERNEL_PACKED, 128, 5, 512)
+            b.set_config(lms.KERNEL_PACKED, 128, 4, 512)
         b.set_config(lms.KERNEL_DIRECT, 128, 5, 512)
         b.smooth(5)
         for i, m in enumerate(meshes):
@@ -407,7 +409,7 @@ def test_batched_config_rejects_unsupported_chunks():
         for chunk in (0, 7, 9, -1):
             with pytest.raises(lms.LmsError):
                 b.set_config(lms.KERNEL_DIRECT, 128, chunk, 512)
-        for chunk in (1, 2, 7, 8):
+        for chunk in (1, 3, 5, 8):
             with pytest.raises(lms.LmsError):
                 b.set_config(lms.KERNEL_PACKED, 128, chunk, 512)
         with pytest.raises(lms.LmsError):
