@@ -272,6 +272,16 @@ int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
    eight tiles per SM, within 128..1024).  The sweep's result depends on the tile
    (it fixes the order).  lms_get_block_tile returns the tile the next sweep uses.  [host] */
 int lms_set_block_tile(lms_handle h, int32_t tile);
+
+/* How LMS_BLOCK_GS sweeps read positions.  on = 0 (default): through L1 from global memory.  on = 1: each
+   CTA copies its tile, the tile's halo (the neighbours of its interior vertices outside the tile), the
+   tile's rows as shared-memory indices and its vertex list into shared memory, sweeps the tile's colour
+   groups there and writes back the tile's interior vertices - used whenever the largest tile with its
+   halo fits in one CTA's shared memory (and needs fewer than 65,536 positions), else the sweep reads
+   global memory.  Results are the same either way (the same in-place order); on GB300 the staged form
+   was slower on every measured mesh (shared memory sized for the largest tile limits the CTAs per SM).
+   [host]  LMS_ERR_ARG. */
+int lms_set_block_staging(lms_handle h, int32_t on);
 int lms_get_block_tile(lms_handle h, int32_t* tile);
 
 /* Where the arithmetic of FP64 Jacobi and coloured GS sweeps (Eq. 1) runs: LMS_FP64_ARITH_* (default

@@ -88,6 +88,7 @@ _SIGS = {
     "lms_block_walk": ([_I32, _P, _P, _P, _P, _I32, _P, _PI32, _PI32], ctypes.c_int),
     "lms_set_fp64_arith": ([_P, _I32], ctypes.c_int),
     "lms_set_block_tile": ([_P, _I32], ctypes.c_int),
+    "lms_set_block_staging": ([_P, _I32], ctypes.c_int),
     "lms_get_block_tile": ([_P, _PI32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
@@ -444,6 +445,10 @@ class Mesh:
     def set_inplace_split(self, threads):
         """GPU threads of INPLACE_STATIC sweeps (0 = default, 1 = sequential Algorithm 1)."""
         _check(_lib().lms_set_inplace_split(self._handle(), int(threads)), "lms_set_inplace_split")
+
+    def set_block_staging(self, on):
+        """lms_set_block_staging: LMS_BLOCK_GS through shared memory (tile + halo) or from global memory."""
+        _check(_lib().lms_set_block_staging(self._handle(), int(on)), "lms_set_block_staging")
 
     def set_block_tile(self, tile):
         """Tile (storage positions) of BLOCK_GS sweeps; 0 = by mesh size."""

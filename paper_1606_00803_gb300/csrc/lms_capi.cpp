@@ -292,6 +292,15 @@ struct lms_mesh_s {
     int32_t* d_blk_verts = nullptr;
     int32_t* d_blk_groups = nullptr;
     int64_t blk_verts_cap = 0, blk_groups_cap = 0;
+    // staged block Gauss-Seidel tables (tile + halo in shared memory); used when block_staged and they fit
+    // (off by default: slower than reading through L1 on the measured meshes)
+    bool block_staged = false;
+    bool st_valid = false;
+    int32_t st_max_slots = 0, st_max_verts = 0, st_max_entries = 0;
+    int4* d_st_tile = nullptr;
+    int32_t *d_st_halo = nullptr, *d_st_lrow = nullptr;
+    uint16_t* d_st_lcol = nullptr;
+    int64_t st_tile_cap = 0, st_halo_cap = 0, st_lrow_cap = 0, st_lcol_cap = 0;
     int32_t fp64_arith = LMS_FP64_ARITH_MIXED3;  // where FP64 sums and means run (fastest on GB300)
 
     ~lms_mesh_s() {
@@ -578,6 +587,47 @@ int ensure_block_tables(lms_mesh_s* h) {
                              cudaMemcpyHostToDevice, h->stream));
     LMS_CUDA(cudaMemcpyAsync(h->d_blk_groups, bt.groups.data(), sizeof(int32_t) * bt.groups.size(),
                              cudaMemcpyHostToDevice, h->stream));
+    // shared-memory tables of the staged kernel, when a tile with its halo fits in a CTA's shared memory
+    h->st_valid = false;
+    lms::BlockStageTables st;
+    int dev = 0, smem_max = 0;
+    if (h->block_staged && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        lms::block_stage_tables(h->n, h->rp.data(), h->ci.data(), h->user_perm.data(), tile, bt, st) == LMS_OK &&
+        lms::block_gs_staged_smem(h->precision, st.max_slots, st.max_verts, st.max_entries) + 2048 <= size_t(smem_max)) {
+        if (st.tile_info.empty()) st.tile_info.assign(4, 0);
+        if (st.halo.empty()) st.halo.assign(1, 0);
+        if (st.lcol.empty()) st.lcol.assign(1, 0);
+        const int64_t ntile = int64_t(st.tile_info.size() / 4);
+        if (ntile > h->st_tile_cap) {
+            LMS_TRY(h->arena.get(&h->d_st_tile, size_t(ntile)));
+            h->st_tile_cap = ntile;
+        }
+        if (int64_t(st.halo.size()) > h->st_halo_cap) {
+            LMS_TRY(h->arena.get(&h->d_st_halo, st.halo.size()));
+            h->st_halo_cap = int64_t(st.halo.size());
+        }
+        if (int64_t(st.lrow.size()) > h->st_lrow_cap) {
+            LMS_TRY(h->arena.get(&h->d_st_lrow, st.lrow.size()));
+            h->st_lrow_cap = int64_t(st.lrow.size());
+        }
+        if (int64_t(st.lcol.size()) > h->st_lcol_cap) {
+            LMS_TRY(h->arena.get(&h->d_st_lcol, st.lcol.size()));
+            h->st_lcol_cap = int64_t(st.lcol.size());
+        }
+        LMS_CUDA(cudaMemcpyAsync(h->d_st_tile, st.tile_info.data(), sizeof(int32_t) * st.tile_info.size(),
+                                 cudaMemcpyHostToDevice, h->stream));
+        LMS_CUDA(cudaMemcpyAsync(h->d_st_halo, st.halo.data(), sizeof(int32_t) * st.halo.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+        LMS_CUDA(cudaMemcpyAsync(h->d_st_lrow, st.lrow.data(), sizeof(int32_t) * st.lrow.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+        LMS_CUDA(cudaMemcpyAsync(h->d_st_lcol, st.lcol.data(), sizeof(uint16_t) * st.lcol.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+        h->st_max_slots = st.max_slots;
+        h->st_max_verts = st.max_verts;
+        h->st_max_entries = st.max_entries;
+        h->st_valid = true;
+    }
     LMS_CUDA(cudaStreamSynchronize(h->stream));  // the host tables die here
     h->block_tc_ofs = bt.tc_ofs;
     h->block_ncolours = bt.ncolours;
@@ -637,6 +687,30 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
 // base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
 int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
     const int src = (base + k1 - 1) & 1;
+    if (mode == LMS_BLOCK_GS && h->block_staged && h->st_valid) {  // one launch per tile colour, staged
+        lms::BlockGsStagedArgs a{};
+        a.xy = h->d_xy[base];
+        a.tile_info = h->d_st_tile;
+        a.halo = h->d_st_halo;
+        a.verts = h->d_blk_verts;
+        a.lrow = h->d_st_lrow;
+        a.lcol = h->d_st_lcol;
+        a.group_ofs = h->d_blk_groups;
+        a.ncolours = h->block_ncolours;
+        a.max_slots = h->st_max_slots;
+        a.max_verts = h->st_max_verts;
+        a.max_entries = h->st_max_entries;
+        a.state = stoppable ? h->d_state : nullptr;
+        a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
+        a.recip = h->d_recip;
+        for (size_t c = 0; c + 1 < h->block_tc_ofs.size(); ++c) {
+            a.tile_begin = h->block_tc_ofs[c];
+            LMS_TRY(check_launch(
+                lms::launch_block_gs_staged(h->precision, a, h->block_tc_ofs[c + 1] - h->block_tc_ofs[c], s),
+                "block_gs_staged"));
+        }
+        return LMS_OK;
+    }
     if (mode == LMS_BLOCK_GS) {  // one launch per tile colour, in place
         lms::BlockGsArgs a{};
         a.row_ptr = h->d_rp;
@@ -1003,6 +1077,16 @@ int lms_set_block_tile(lms_handle h, int32_t tile) {
     LMS_TRY(finish_stats(h));
     if (tile != h->block_tile_req) {
         h->block_tile_req = tile;
+        h->graphs.clear();
+    }
+    return LMS_OK;
+}
+
+int lms_set_block_staging(lms_handle h, int32_t on) {
+    if (!h || (on != 0 && on != 1)) return LMS_ERR_ARG;
+    if (h->block_staged != (on != 0)) {
+        h->block_staged = on != 0;
+        h->block_valid = false;  // the staged tables are built with the block tables when staging is on
         h->graphs.clear();
     }
     return LMS_OK;

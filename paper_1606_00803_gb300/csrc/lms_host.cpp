@@ -556,6 +556,55 @@ int block_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, cons
     return LMS_OK;
 }
 
+int block_stage_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* new_to_old,
+                       int32_t tile, const BlockTables& bt, BlockStageTables& out) {
+    if (n <= 0 || !row_ptr || !col_idx || !new_to_old || tile < 1) return LMS_ERR_ARG;
+    const int32_t nc = bt.ncolours;
+    const size_t listed = bt.groups.size() / (static_cast<size_t>(nc) + 1);
+    std::vector<int32_t> pos(n);
+    for (int32_t k = 0; k < n; ++k) pos[new_to_old[k]] = k;
+    std::vector<int32_t> seen(n, -1), slot(n, 0);  // seen[u] = listed tile that last put u in its halo
+    out.tile_info.clear();
+    out.halo.clear();
+    out.lrow.assign(1, 0);
+    out.lcol.clear();
+    out.lrow.reserve(bt.verts.size() + 1);
+    out.max_slots = 0;
+    for (size_t L = 0; L < listed; ++L) {
+        const int32_t i0 = bt.groups[L * (nc + 1)], i1 = bt.groups[L * (nc + 1) + nc];
+        const int32_t t = bt.verts[i0] / tile;
+        const int32_t x = t * tile, y = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(x) + tile, n));
+        const int32_t z = static_cast<int32_t>(out.halo.size());
+        for (int32_t i = i0; i < i1; ++i) {
+            const int32_t v = new_to_old[bt.verts[i]];
+            for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                const int32_t u = pos[col_idx[e]];
+                int64_t local;
+                if (u >= x && u < y) {
+                    local = u - x;
+                } else {
+                    if (seen[u] != static_cast<int32_t>(L)) {
+                        seen[u] = static_cast<int32_t>(L);
+                        slot[u] = static_cast<int32_t>(out.halo.size()) - z;
+                        out.halo.push_back(u);
+                    }
+                    local = static_cast<int64_t>(y - x) + slot[u];
+                }
+                if (local >= 65536) return LMS_ERR_ARG;
+                out.lcol.push_back(static_cast<uint16_t>(local));
+            }
+            out.lrow.push_back(static_cast<int32_t>(out.lcol.size()));
+        }
+        const int32_t w = static_cast<int32_t>(out.halo.size());
+        out.tile_info.insert(out.tile_info.end(), {x, y, z, w});
+        out.max_slots = std::max(out.max_slots, (y - x) + (w - z));
+        out.max_verts = std::max(out.max_verts, i1 - i0);
+        out.max_entries = std::max(out.max_entries, out.lrow[i1] - out.lrow[i0]);
+        if (out.max_slots >= 65536) return LMS_ERR_ARG;
+    }
+    return LMS_OK;
+}
+
 }  // namespace lms
 
 extern "C" {

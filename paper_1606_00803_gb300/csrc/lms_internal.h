@@ -45,6 +45,24 @@ struct BlockTables {
 int block_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                  const int32_t* new_to_old, int32_t tile, BlockTables& out);
 
+// Shared-memory tables of the staged block Gauss-Seidel sweep, built from BlockTables for the same storage
+// order and tile: per listed tile its position range [x, y) and halo range [z, w) in `halo` (storage
+// positions of the neighbours of its interior vertices outside the tile, in first-seen order); per entry
+// of BlockTables::verts the start of its row in `lcol` (lrow, one more entry than verts), and in lcol each
+// row's neighbours, in stored row order, as indices into the tile's shared-memory copy: position p of the
+// tile -> p - x, halo vertex j -> (y - x) + j.  max_slots = largest (y - x) + (w - z) over the tiles.
+struct BlockStageTables {
+    std::vector<int32_t> tile_info;  // 4 ints per listed tile: x, y, z, w
+    std::vector<int32_t> halo, lrow;
+    std::vector<uint16_t> lcol;
+    int32_t max_slots = 0;
+    int32_t max_verts = 0;    // largest count of interior vertices in a tile
+    int32_t max_entries = 0;  // largest count of lcol entries of a tile
+};
+// Returns LMS_ERR_ARG when a tile with its halo needs 65,536 slots or more (16-bit local indices).
+int block_stage_tables(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* new_to_old,
+                       int32_t tile, const BlockTables& bt, BlockStageTables& out);
+
 // Set the message reported with LMS_ERR_CUDA and friends (thread-local).
 void set_error_detail(const std::string& s);
 const std::string& error_detail();
@@ -104,6 +122,30 @@ struct BlockGsArgs {
     const double* recip;           // FP64 reciprocal table
 };
 cudaError_t launch_block_gs(int precision, const BlockGsArgs& a, int32_t n_tiles, cudaStream_t stream);
+
+// Staged block Gauss-Seidel (k_block_gs_staged): as k_block_gs, but each CTA copies its tile and the
+// tile's halo into shared memory, sweeps the colour groups there and writes back the tile's interior
+// vertices.  Tables from BlockStageTables.
+struct BlockGsStagedArgs {
+    void* xy;                      // double2 / float2 positions, updated in place
+    const int4* tile_info;         // per listed tile: first, end position; first, end halo entry
+    const int32_t* halo;
+    const int32_t* verts;          // storage positions of the interior vertices in block order
+    const int32_t* lrow;           // per verts entry: first local neighbour index in lcol (+1 entry)
+    const uint16_t* lcol;          // local neighbour indices into the tile's shared-memory copy
+    const int32_t* group_ofs;      // [listed tile][ncolours + 1]: offsets of the tile's colour groups in verts
+    int32_t ncolours;
+    int32_t tile_begin;            // listed tile handled by block 0 of this launch
+    int32_t max_slots;             // shared-memory positions per CTA (largest tile + halo)
+    int32_t max_verts;             // largest interior vertex count of a tile
+    int32_t max_entries;           // largest local-row entry count of a tile
+    const DevState* state;         // stop flag (NULL: never stop)
+    unsigned long long* disp2;     // max squared displacement (NULL: off)
+    const double* recip;           // FP64 reciprocal table
+};
+cudaError_t launch_block_gs_staged(int precision, const BlockGsStagedArgs& a, int32_t n_tiles, cudaStream_t stream);
+// bytes of dynamic shared memory per CTA of k_block_gs_staged
+size_t block_gs_staged_smem(int precision, int32_t max_slots, int32_t max_verts, int32_t max_entries);
 
 // Tile-staged sweep (lms_staged.cu): items[i] = (first vertex, end vertex, first CSR entry, end entry)
 // of a tile; tiles never cross a mesh or a colour range.  row_ptr, col_idx and bnd_bits must have at

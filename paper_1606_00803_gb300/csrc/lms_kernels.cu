@@ -22,6 +22,7 @@
 //         unit size; neighbour sums are Kahan-compensated and the mean is the
 //         compensated sum times the round-to-nearest reciprocal of the count
 //         (within 1.5 ulp); quality sums are reduced in FP64.
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <type_traits>
@@ -230,6 +231,100 @@ __global__ void __launch_bounds__(256) k_block_gs(BlockGsArgs a) {
             xy[v] = r;
         }
         __syncthreads();
+    }
+    if (want) record_disp(a.disp2, dmax);
+}
+
+// Staged block Gauss-Seidel: block b takes listed tile a.tile_begin + b and copies into shared memory the
+// tile's positions, its halo (the neighbours of its interior vertices outside the tile), and the tile's
+// local rows (neighbours as shared-memory indices) and vertex list; it then sweeps the tile's colour groups
+// in turn entirely on chip (a block barrier between groups) and writes back the tile's interior vertices.
+// Tiles of one tile colour share no edge between interior vertices, so nothing a CTA reads into its halo
+// is written by another CTA of the launch, and the launch equals the in-place sweep over its tiles in
+// block order: FP64 bit-identical to the oracle (sums in stored row order, first term a copy, the
+// table-driven division), FP32 with Kahan sums.
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_block_gs_staged(BlockGsStagedArgs a) {
+    if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
+    using V = typename std::conditional<FP64, double2, float2>::type;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    // layout: positions [max_slots] | row starts [max_verts + 1] (int32, relative to the tile's first
+    // entry) | vertex positions in the tile [max_verts] (uint16) | local neighbour indices [max_entries]
+    V* s_pos = reinterpret_cast<V*>(s_raw);
+    int32_t* s_row = reinterpret_cast<int32_t*>(s_pos + a.max_slots);
+    uint16_t* s_vert = reinterpret_cast<uint16_t*>(s_row + a.max_verts + 1);
+    uint16_t* s_col = s_vert + a.max_verts;
+    __shared__ double s_recip[kMaxRecipDeg + 1];
+    if (FP64)
+        for (int i = threadIdx.x; i <= kMaxRecipDeg; i += blockDim.x) s_recip[i] = a.recip[i];
+    V* xy = static_cast<V*>(a.xy);
+    const int32_t tile = a.tile_begin + static_cast<int32_t>(blockIdx.x);
+    const int4 ti = __ldg(a.tile_info + tile);
+    const int32_t* g = a.group_ofs + static_cast<int64_t>(tile) * (a.ncolours + 1);
+    const int32_t i0 = __ldg(g), i1 = __ldg(g + a.ncolours);
+    const int32_t T = ti.y - ti.x, H = ti.w - ti.z, nv = i1 - i0;
+    const int32_t r0 = __ldg(a.lrow + i0), ne = __ldg(a.lrow + i1) - r0;
+    const bool fits = T + H <= a.max_slots && nv <= a.max_verts && ne <= a.max_entries;
+    if (!fits) {  // never by construction (the limits are maxima over the tiles); counted in debug builds
+        (void)LMS_CHECK(false);
+        return;
+    }
+    for (int32_t i = threadIdx.x; i < T; i += blockDim.x) s_pos[i] = xy[ti.x + i];
+    for (int32_t j = threadIdx.x; j < H; j += blockDim.x) s_pos[T + j] = xy[__ldg(a.halo + ti.z + j)];
+    for (int32_t i = threadIdx.x; i <= nv; i += blockDim.x) s_row[i] = __ldg(a.lrow + i0 + i) - r0;
+    for (int32_t i = threadIdx.x; i < nv; i += blockDim.x) s_vert[i] = static_cast<uint16_t>(__ldg(a.verts + i0 + i) - ti.x);
+    for (int32_t e = threadIdx.x; e < ne; e += blockDim.x) s_col[e] = __ldg(a.lcol + r0 + e);
+    __syncthreads();
+    const bool want = a.disp2 != nullptr;
+    double dmax = 0.0;
+    for (int32_t c = 0; c < a.ncolours; ++c) {
+        const int32_t b = __ldg(g + c) - i0, end = __ldg(g + c + 1) - i0;
+        for (int32_t i = b + static_cast<int32_t>(threadIdx.x); i < end; i += static_cast<int32_t>(blockDim.x)) {
+            const int32_t lv = s_vert[i];
+            const int32_t e0 = s_row[i], e1 = s_row[i + 1];
+            const V o = s_pos[lv];
+            V r;
+            if constexpr (FP64) {
+                double sx = 0.0, sy = 0.0;
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int32_t l = s_col[e];
+                    if (!LMS_CHECK(l < T + H)) continue;
+                    const V p = s_pos[l];
+                    if (e == e0) {
+                        sx = plus_zero(p.x);
+                        sy = plus_zero(p.y);
+                    } else {
+                        sx = __dadd_rn(sx, p.x);
+                        sy = __dadd_rn(sy, p.y);
+                    }
+                }
+                r.x = div_by_count(sx, e1 - e0, s_recip);
+                r.y = div_by_count(sy, e1 - e0, s_recip);
+            } else {
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int32_t l = s_col[e];
+                    if (!LMS_CHECK(l < T + H)) continue;
+                    const V p = s_pos[l];
+                    kahan_add(sx, cx, p.x);
+                    kahan_add(sy, cy, p.y);
+                }
+                r.x = mean_f32(sx, cx, e1 - e0);
+                r.y = mean_f32(sy, cy, e1 - e0);
+            }
+            if (want) {
+                const double ex = static_cast<double>(r.x) - static_cast<double>(o.x);
+                const double ey = static_cast<double>(r.y) - static_cast<double>(o.y);
+                dmax = fmax(dmax, __fma_rn(ex, ex, __dmul_rn(ey, ey)));
+            }
+            s_pos[lv] = r;
+        }
+        __syncthreads();
+    }
+    // write back the tile's interior vertices (the only positions the tile changed)
+    for (int32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+        const int32_t lv = s_vert[i];
+        xy[ti.x + lv] = s_pos[lv];
     }
     if (want) record_disp(a.disp2, dmax);
 }
@@ -1066,6 +1161,26 @@ cudaError_t launch_block_gs(int precision, const BlockGsArgs& a, int32_t n_tiles
     else
         k_block_gs<false><<<n_tiles, 256, 0, stream>>>(a);
     return cudaGetLastError();
+}
+
+size_t block_gs_staged_smem(int precision, int32_t max_slots, int32_t max_verts, int32_t max_entries) {
+    const size_t pos = static_cast<size_t>(std::max(1, max_slots)) * (precision == LMS_FP64 ? sizeof(double2) : sizeof(float2));
+    return pos + 4 * (static_cast<size_t>(max_verts) + 1) + 2 * static_cast<size_t>(max_verts) +
+           2 * static_cast<size_t>(max_entries) + 16;
+}
+
+cudaError_t launch_block_gs_staged(int precision, const BlockGsStagedArgs& a, int32_t n_tiles, cudaStream_t stream) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const size_t smem = block_gs_staged_smem(precision, a.max_slots, a.max_verts, a.max_entries);
+    cudaError_t e;
+    if (precision == LMS_FP64) {
+        e = cudaFuncSetAttribute(k_block_gs_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess) k_block_gs_staged<true><<<n_tiles, 256, smem, stream>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_block_gs_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess) k_block_gs_staged<false><<<n_tiles, 256, smem, stream>>>(a);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_add_selftest(int32_t count, const double* a, const double* b, double* s, cudaStream_t stream) {

@@ -23,32 +23,61 @@ def mesh():
     return meshgen.workload(1, side=70)  # ~5k vertices: many tiles, a ragged last tile
 
 
-@pytest.mark.parametrize("ordering", [lms.ORI, lms.BFS, lms.RDR])
+@pytest.mark.parametrize("staged", [True, False])
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.BFS, lms.RDR, lms.RANDOM])
 @pytest.mark.parametrize("tile", [32, 96, 1000])
-def test_fp64_block_gs_bit_exact(mesh, ordering, tile):
+def test_fp64_block_gs_bit_exact(mesh, ordering, tile, staged):
+    """Both forms of the sweep - tile and halo staged in shared memory, or read from global memory - are
+    the oracle's in-place sweep in block order, bit for bit."""
     m = mesh
-    p = oracle.order(m, ordering)
+    p = oracle.order(m, ordering, seed=3)
     want, _, _ = oracle.block_gs_smooth(m, p, tile, 12)
     with lms.Mesh.from_dict(m, lms.FP64) as g:
-        g.reorder(ordering)
+        g.reorder(ordering, seed=3)
         g.set_block_tile(tile)
+        g.set_block_staging(staged)
         assert g.block_tile() == tile
         g.smooth(12, mode=lms.BLOCK_GS)
         got = g.coords()
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("staged", [True, False])
 @pytest.mark.parametrize("tile", [64, 512])
-def test_fp32_block_gs_within_tolerance(mesh, tile):
+def test_fp32_block_gs_within_tolerance(mesh, tile, staged):
     m = mesh
     p = oracle.order(m, oracle.RDR)
     want, _, _ = oracle.block_gs_smooth(m, p, tile, 100)
     with lms.Mesh.from_dict(m, lms.FP32) as g:
         g.reorder(lms.RDR)
         g.set_block_tile(tile)
+        g.set_block_staging(staged)
         g.smooth(100, mode=lms.BLOCK_GS)
         got = g.coords()
     assert np.abs(got - want).max() <= TOL32 * diag(m)
+
+
+def test_block_gs_tile_too_large_for_shared_memory_falls_back():
+    """A tile whose halo does not fit in one CTA's shared memory (a random order scatters the neighbours of
+    a 40,000-position tile over the whole mesh) runs from global memory with the same result."""
+    m = meshgen.workload(1, side=260)
+    p = oracle.order(m, oracle.RANDOM, seed=5)
+    want, _, _ = oracle.block_gs_smooth(m, p, 40000, 3)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(lms.RANDOM, seed=5)
+        g.set_block_tile(40000)
+        g.set_block_staging(1)
+        g.smooth(3, mode=lms.BLOCK_GS)
+        got = g.coords()
+    assert np.array_equal(got, want)
+
+
+def test_block_staging_rejects_bad_values():
+    m = meshgen.workload(0)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        for bad in (-1, 2):
+            with pytest.raises(lms.LmsError):
+                g.set_block_staging(bad)
 
 
 def test_block_gs_mixed_with_other_modes_and_automatic_tile():

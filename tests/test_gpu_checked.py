@@ -45,7 +45,9 @@ for o in (lms.ORI, lms.RDR, lms.BFS, lms.BRDR):
             runs = [("jacobi", lambda: g.smooth(9), want_j),
                     ("gs", lambda: g.smooth(3, mode=lms.COLORED_GS), want_gs),
                     ("inplace1", lambda: (g.set_inplace_split(1), g.smooth(2, mode=lms.INPLACE_STATIC)), want_seq),
-                    ("block_gs", lambda: (g.set_block_tile(96), g.smooth(4, mode=lms.BLOCK_GS)), want_blk)]
+                    ("block_gs", lambda: (g.set_block_tile(96), g.smooth(4, mode=lms.BLOCK_GS)), want_blk),
+                    ("block_gs_staged", lambda: (g.set_block_staging(1), g.smooth(4, mode=lms.BLOCK_GS),
+                                                 g.set_block_staging(0)), want_blk)]
             for name, run, want in runs:
                 g.set_coords(xy0)
                 run()
