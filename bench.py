@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--meshes", type=int, default=512)
     ap.add_argument("--full", action="store_true", help="also time the 4096 x 4096 workload (FP64 vs FP32)")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no per-ordering table)")
+    ap.add_argument("--profile-fp64", type=int, choices=[1, 4],
+                    help="profiling driver: the 1024 x 1024 (1) or 4096 x 4096 (4) mesh in FP64, RDR, 5 Jacobi "
+                         "sweeps (run it under ncu); prints no JSON")
     ap.add_argument("--profile-ordering", choices=[o for o, _ in ORDERINGS],
                     help="profiling driver: the 4096 x 4096 mesh in FP32 under one ordering, 5 Jacobi sweeps "
                          "(run it under ncu to read DRAM bytes and L2 hit rate per ordering); prints no JSON")
@@ -923,8 +926,27 @@ def profile_ordering(name):
         log("profile-ordering %s: %d vertices, 5 sweeps, %.4f ms device time" % (name, m["n"], g.last_stats()["ms"]))
 
 
+def profile_fp64(workload):
+    """5 FP64 Jacobi sweeps (one launch each) of a single mesh in the RDR ordering."""
+    import torch
+    import meshgen
+    import paper_1606_00803_gb300 as lms
+    m = meshgen.workload(workload)
+    with lms.Mesh.from_dict(m, lms.FP64) as g:
+        g.reorder(lms.RDR)
+        g.smooth(5)
+        torch.cuda.synchronize()
+        log("profile-fp64 workload %d: %d vertices, 5 sweeps, %.4f ms device time" % (workload, m["n"],
+                                                                                       g.last_stats()["ms"]))
+
+
 def main():
     args = parse_args()
+    if args.profile_fp64:
+        import __graft_entry__
+        __graft_entry__.build()
+        profile_fp64(args.profile_fp64)
+        return
     if args.profile_ordering:
         import __graft_entry__
         __graft_entry__.build()
