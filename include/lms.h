@@ -52,8 +52,8 @@ extern "C" {
 /* precision of the stored coordinates and of the sweep arithmetic */
 #define LMS_FP64 0 /* double2 coordinates, FP64 sums and division (results equal the FP64 sequential sums) */
 #define LMS_FP32 1 /* float2 coordinates relative to the bounding-box centre, scaled by the larger box
-                      side; compensated (Kahan) FP32 neighbour sums, mean by the rounded reciprocal of
-                      the count; quality reduced in FP64 */
+                      side; compensated (Kahan) FP32 neighbour sums, mean by a correctly rounded
+                      division by the count; quality reduced in FP64 */
 
 /* vertex orderings (Section 5.2.1 compares ORI, BFS and RDR; Fig. 1 adds a random one) */
 #define LMS_ORI 0    /* original order: identity permutation */

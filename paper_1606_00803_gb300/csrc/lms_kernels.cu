@@ -20,8 +20,8 @@
 //         and this is ~3 FP64 operations instead of a full division.
 //   FP32  coordinates are relative to the bounding-box centre and scaled to
 //         unit size; neighbour sums are Kahan-compensated and the mean is the
-//         compensated sum times the round-to-nearest reciprocal of the count
-//         (within 1.5 ulp); quality sums are reduced in FP64.
+//         compensated sum divided by the count, correctly rounded; quality sums
+//         are reduced in FP64.
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
