@@ -53,7 +53,7 @@ extern "C" {
 #define LMS_FP64 0 /* double2 coordinates, FP64 sums and division (results equal the FP64 sequential sums) */
 #define LMS_FP32 1 /* float2 coordinates relative to the bounding-box centre, scaled by the larger box
                       side; compensated (Kahan) FP32 neighbour sums, mean by a correctly rounded
-                      division by the count; quality reduced in FP64 */
+                      division by the count (lms_selftest_div32); quality reduced in FP64 */
 
 /* vertex orderings (Section 5.2.1 compares ORI, BFS and RDR; Fig. 1 adds a random one) */
 #define LMS_ORI 0    /* original order: identity permutation */
@@ -377,6 +377,15 @@ const char* lms_last_error_detail(void);
  * q[i] must equal the IEEE quotient.  Host arrays of `count` entries.
  */
 int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double* q);
+
+/*
+ * Diagnostic of the FP32 sweeps' mean: q[i] = s[i] / d[i] (1 <= d[i] <= 64) computed on the device by
+ * the routine every FP32 sweep uses (rounded reciprocal, product, one fused correction).  For finite s[i]
+ * with |s[i]| >= 2^-100, and for zeros, q[i] must equal the IEEE round-to-nearest quotient; below 2^-100
+ * it is within one ulp of it.  Host arrays of `count` entries.  LMS_ERR_ARG (negative count, NULL, d[i]
+ * < 1), LMS_ERR_CUDA.
+ */
+int lms_selftest_div32(int32_t count, const float* s, const int32_t* d, float* q);
 
 /*
  * Diagnostics of the FP64 sweep's integer-pipe arithmetic (LMS_FP64_ARITH_INT): s[i] = a[i] + b[i] and

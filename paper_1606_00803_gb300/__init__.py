@@ -92,6 +92,7 @@ _SIGS = {
     "lms_get_block_tile": ([_P, _PI32], ctypes.c_int),
     "lms_destroy": ([_P], None),
     "lms_selftest_div64": ([_I32, _P, _P, _P], ctypes.c_int),
+    "lms_selftest_div32": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_add64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_divint64": ([_I32, _P, _P, _P], ctypes.c_int),
     "lms_selftest_timeout": ([_I32], ctypes.c_int),
@@ -344,6 +345,14 @@ def selftest_divint64(s, d):
     s, d = _arr(s, np.float64), _arr(d, np.int32)
     q = np.empty_like(s)
     _check(_lib().lms_selftest_divint64(len(s), _ptr(s), _ptr(d), _ptr(q)), "lms_selftest_divint64")
+    return q
+
+
+def selftest_div32(s, d):
+    """lms_selftest_div32: s / d by the FP32 sweeps' mean routine on the device (float32 arrays)."""
+    sa, da = _arr(s, np.float32), _arr(d, np.int32)
+    q = np.empty(len(sa), np.float32)
+    _check(_lib().lms_selftest_div32(len(sa), _ptr(sa), _ptr(da), _ptr(q)), "lms_selftest_div32")
     return q
 
 

@@ -1344,6 +1344,31 @@ int lms_selftest_div64(int32_t count, const double* s, const int32_t* d, double*
     return selftest_div(count, s, d, q, false);
 }
 
+int lms_selftest_div32(int32_t count, const float* s, const int32_t* d, float* q) {
+    if (count < 0 || (count > 0 && (!s || !d || !q))) return LMS_ERR_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (d[i] < 1) return LMS_ERR_ARG;
+    if (count == 0) return LMS_OK;
+    Arena A;
+    float *ds = nullptr, *dq = nullptr;
+    int32_t* dd = nullptr;
+    int rc = LMS_OK;
+    if ((rc = A.get(&ds, count)) || (rc = A.get(&dq, count)) || (rc = A.get(&dd, count))) {
+        A.release_all();
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(ds, s, 4 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, d, 4 * size_t(count), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = lms::launch_div32_selftest(count, ds, dd, dq, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(q, dq, 4 * size_t(count), cudaMemcpyDeviceToHost);
+    A.release_all();
+    if (e != cudaSuccess) {
+        lms::set_error_detail(std::string("selftest: ") + cudaGetErrorString(e));
+        return LMS_ERR_CUDA;
+    }
+    return LMS_OK;
+}
+
 int lms_selftest_divint64(int32_t count, const double* s, const int32_t* d, double* q) {
     return selftest_div(count, s, d, q, true);
 }

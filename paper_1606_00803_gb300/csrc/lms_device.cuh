@@ -53,11 +53,22 @@ __device__ __forceinline__ double div_by_count(double s, int32_t d, const double
     return __ddiv_rn(s, static_cast<double>(d));
 }
 
-// FP32 mean of a compensated sum: the compensated sum s - c divided by the neighbour count, correctly
-// rounded (IEEE division).  The division's single rounding, against 1.5 ulp for a multiply by the
-// rounded reciprocal, is most of the error an FP32 sweep adds to the stored positions.
+// FP32 mean of a compensated sum: a = s - c divided by the neighbour count d.  y = RN(1/d), q = RN(a*y),
+// then one fused correction q + RN(a - d*q)*y (Markstein's division refinement, as for the FP64 sweep):
+// the correctly rounded quotient for every |a| >= 2^-100 - every sum of a mesh normalised to unit size -
+// and zero for a zero sum (the select keeps the sign of a negative zero); within one ulp below 2^-100
+// (subnormal quotients).  The single rounding, against 1.5 ulp for a multiply by the rounded reciprocal,
+// is most of the error an FP32 sweep adds to the stored positions.  Two FMAs and no branch: an IEEE
+// division, or a branch to one for special values, costs 1-4% of a batched sweep.  lms_selftest_div32
+// checks it against IEEE division.
 __device__ __forceinline__ float mean_f32(float s, float c, int32_t d) {
-    return __fdiv_rn(__fsub_rn(s, c), static_cast<float>(d));
+    const float a = __fsub_rn(s, c);
+    const float df = static_cast<float>(d);
+    const float y = __frcp_rn(df);
+    const float q = __fmul_rn(a, y);
+    const float r = __fmaf_rn(-q, df, a);
+    const float m = __fmaf_rn(r, y, q);
+    return a == 0.f ? a : m;
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {

@@ -317,6 +317,8 @@ cudaError_t launch_batch_store_xy(int32_t n_items, const int2* items, const int3
                                   const double* mesh_cs, const uint32_t* bnd_bits, const double* fixed_xy,
                                   cudaStream_t stream);
 
+// Diagnostic: q[i] = s[i] / d[i] by the FP32 sweeps' mean (mean_f32 with c = 0).
+cudaError_t launch_div32_selftest(int32_t count, const float* s, const int32_t* d, float* q, cudaStream_t stream);
 // Diagnostic: s[i] = RN(a[i] + b[i]) by the integer-pipe addition of the FP64 sweep (add_rn_int).
 cudaError_t launch_add_selftest(int32_t count, const double* a, const double* b, double* s, cudaStream_t stream);
 // Diagnostic: q[i] = s[i] / d[i] by the integer-pipe division of LMS_FP64_ARITH_INT (div_rn_int).

@@ -20,8 +20,9 @@
 //         and this is ~3 FP64 operations instead of a full division.
 //   FP32  coordinates are relative to the bounding-box centre and scaled to
 //         unit size; neighbour sums are Kahan-compensated and the mean is the
-//         compensated sum divided by the count, correctly rounded; quality sums
-//         are reduced in FP64.
+//         compensated sum divided by the count, correctly rounded (the same
+//         refinement of a rounded reciprocal as FP64); quality sums are reduced
+//         in FP64.
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
@@ -871,6 +872,12 @@ __global__ void k_div_selftest(int32_t count, const double* __restrict__ s, cons
     if (i < count) q[i] = div_by_count(s[i], d[i], recip);
 }
 
+__global__ void k_div32_selftest(int32_t count, const float* __restrict__ s, const int32_t* __restrict__ d,
+                                 float* __restrict__ q) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) q[i] = mean_f32(s[i], 0.f, d[i]);
+}
+
 __global__ void k_add_selftest(int32_t count, const double* __restrict__ a, const double* __restrict__ b,
                                double* __restrict__ s) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1181,6 +1188,12 @@ cudaError_t launch_block_gs_staged(int precision, const BlockGsStagedArgs& a, in
         if (e == cudaSuccess) k_block_gs_staged<false><<<n_tiles, 256, smem, stream>>>(a);
     }
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_div32_selftest(int32_t count, const float* s, const int32_t* d, float* q, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    k_div32_selftest<<<blocks_for(count, 256), 256, 0, stream>>>(count, s, d, q);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_add_selftest(int32_t count, const double* a, const double* b, double* s, cudaStream_t stream) {

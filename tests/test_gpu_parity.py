@@ -56,6 +56,33 @@ def test_division_selftest_matches_ieee():
     assert np.array_equal(q.view(np.uint64), (s / d).view(np.uint64))
 
 
+def test_fp32_mean_selftest_matches_ieee():
+    """The FP32 sweeps' mean (rounded reciprocal, product, one fused correction) is the IEEE quotient bit
+    for bit on 4M cases across the exponent range of FP32 neighbour sums, exact multiples and their
+    neighbours, signed zeros and values near the largest finite one; for sums below 2^-100 (subnormal
+    quotients, which no normalised mesh produces) it is within one ulp."""
+    rng = np.random.default_rng(1)
+    n = 4_000_000
+    d = rng.integers(1, 65, size=n).astype(np.int32)
+    e = rng.integers(-40, 20, size=n)
+    s = (rng.uniform(-2, 2, size=n) * np.exp2(e)).astype(np.float32)
+    k = np.arange(2000, dtype=np.float32)
+    s[:2000] = k * d[:2000].astype(np.float32) * np.float32(0.125)           # exact quotients
+    s[2000:4000] = np.nextafter(s[:2000], np.float32(np.inf))                 # their neighbours
+    s[4000:5000] = 0.0
+    s[5000:6000] = -0.0
+    tiny = rng.uniform(-1, 1, 10000) * np.exp2(rng.integers(-149, -60, 10000).astype(np.float64))
+    s[6000:16000] = tiny.astype(np.float32)
+    s[16000:17000] = np.float32(3.0e38) * rng.uniform(-1, 1, 1000).astype(np.float32)
+    q = lms.selftest_div32(s, d)
+    want = (s / d.astype(np.float32)).astype(np.float32)
+    exact = (np.abs(s) >= np.float32(2.0 ** -100)) | (s == 0)
+    assert np.array_equal(q[exact].view(np.uint32), want[exact].view(np.uint32))
+    # below 2^-100 (subnormal quotients): within one ulp, same sign
+    qi, wi = q[~exact].view(np.int32).astype(np.int64), want[~exact].view(np.int32).astype(np.int64)
+    assert np.all(np.abs(qi - wi) <= 1)
+
+
 def test_config0_fp64_jacobi_bit_exact():
     m = meshgen.workload(0)
     want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 10)
