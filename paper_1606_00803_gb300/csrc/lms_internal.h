@@ -260,6 +260,28 @@ struct PackedArgs {
 // chunk = ids per step: 2, 4 or 6
 cudaError_t launch_batch_sweep_packed(const PackedArgs& a, int block, int chunk, int grid, cudaStream_t stream);
 int batch_packed_occupancy(int block, int chunk);  // resident CTAs per SM (0 on error)
+// Single-mesh FP32 Jacobi sweep over packed rows (k_sweep_packed_mesh): row_words[v] = (first id pair of v's row
+// - block_pbase[v >> kPackedBlockShift]) | neighbour count << kPackedDegreeShift | boundary << 31, with
+// block_pbase[b] = first id pair of the rows of storage positions [b << kPackedBlockShift, ...); id_pairs
+// holds every interior row, farthest neighbour first, padded to an even length with -1.  Rows of at most
+// kMaxPackedDegree entries.
+constexpr int kPackedBlockShift = 12;
+struct PackedMeshArgs {
+    const int32_t* row_words;
+    const int32_t* block_pbase;
+    const int2* id_pairs;
+    const void* src;               // float2 positions read
+    void* dst;                     // float2 positions written
+    const int2* items;             // work-queue tiles (first vertex, end vertex)
+    int32_t n_items;
+    int32_t* queue;                // work-queue counter for this launch
+    int32_t n_vertices;            // vertices addressable by the ids (bounds checks of debug builds)
+    const DevState* state;         // stop flag (NULL: never stop)
+    unsigned long long* disp2;     // max squared displacement (NULL: off)
+};
+cudaError_t launch_sweep_packed_mesh(const PackedMeshArgs& a, int block, int grid, cudaStream_t stream);
+int sweep_packed_mesh_occupancy(int block);  // resident CTAs per SM (0 on error)
+
 // out[2 pstart[v] ...] = row v of (row_ptr, col_idx) padded with -1 to 2 (pstart[v + 1] - pstart[v]) ids
 cudaError_t launch_pad_rows(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* pstart,
                             int32_t* out, cudaStream_t stream);

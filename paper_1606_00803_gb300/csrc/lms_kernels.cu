@@ -538,6 +538,78 @@ __global__ void __launch_bounds__(512) k_batch_sweep_packed(PackedArgs a) {
     }
 }
 
+// Single-mesh FP32 Jacobi sweep over packed rows: as k_batch_sweep_packed, but a row word's offset is
+// relative to the first id pair of the vertex's block of 2^kPackedBlockShift storage positions
+// (block_pbase), so any mesh size and any tiling fit one table; the rows of the id-pair array are stored
+// farthest neighbour first.  Rounds are uniform across the block (every lane takes part in the
+// displacement's warp reduction); honours the stop flag; records the largest displacement when asked (old
+// position loaded before the gathers).
+template <int PAIRS>
+__global__ void __launch_bounds__(512) k_sweep_packed_mesh(PackedMeshArgs a) {
+    __shared__ int32_t s_item[2];
+    if (a.state != nullptr && *reinterpret_cast<const volatile int32_t*>(&a.state->stop)) return;
+    const float2* src = static_cast<const float2*>(a.src);
+    float2* dst = static_cast<float2*>(a.dst);
+    const bool want_disp = a.disp2 != nullptr;
+    int buf = 0;
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    for (;;) {
+        const int32_t item = s_item[buf];
+        if (item >= a.n_items) break;
+        if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(a.queue, 1);
+        const int2 r = __ldg(a.items + item);
+        int32_t vn = r.x + static_cast<int32_t>(threadIdx.x);
+        int32_t wn = vn < r.y ? __ldg(a.row_words + vn) : -1;
+        int32_t bn = vn < r.y ? __ldg(a.block_pbase + (vn >> kPackedBlockShift)) : 0;
+        for (int32_t base = r.x; base < r.y; base += blockDim.x) {  // uniform rounds
+            const int32_t v = base + static_cast<int32_t>(threadIdx.x);
+            const int32_t w = wn, pb = bn;
+            vn = v + static_cast<int32_t>(blockDim.x);
+            wn = vn < r.y ? __ldg(a.row_words + vn) : -1;
+            bn = vn < r.y ? __ldg(a.block_pbase + (vn >> kPackedBlockShift)) : 0;
+            double d2 = 0.0;
+            if (w >= 0) {  // inside the tile (w = -1 past its end) and not a boundary vertex
+                float2 o = make_float2(0.f, 0.f);
+                if (want_disp) o = src[v];
+                const int32_t d = (w >> kPackedDegreeShift) & kPackedDegreeMask;
+                const int32_t q0 = pb + (w & kPackedOffsetMask), q1 = q0 + ((d + 1) >> 1);
+                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+                for (int32_t q = q0; q < q1; q += PAIRS) {
+                    int32_t u[2 * PAIRS];
+                    float2 p[2 * PAIRS];
+#pragma unroll
+                    for (int g = 0; g < PAIRS; ++g) {
+                        const int2 x = q + g < q1 ? __ldg(a.id_pairs + q + g) : make_int2(-1, -1);
+                        u[2 * g] = x.x;
+                        u[2 * g + 1] = x.y;
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2 * PAIRS; ++g)
+                        if (u[g] >= 0 && !LMS_CHECK(u[g] < a.n_vertices)) u[g] = -1;
+#pragma unroll
+                    for (int g = 0; g < 2 * PAIRS; ++g) p[g] = u[g] >= 0 ? __ldg(src + u[g]) : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int g = 0; g < 2 * PAIRS; ++g)
+                        if (u[g] >= 0) {
+                            kahan_add(sx, cx, p[g].x);
+                            kahan_add(sy, cy, p[g].y);
+                        }
+                }
+                const float2 m = make_float2(mean_f32(sx, cx, d), mean_f32(sy, cy, d));
+                if (want_disp) {
+                    const double ex = static_cast<double>(__fsub_rn(m.x, o.x)), ey = static_cast<double>(__fsub_rn(m.y, o.y));
+                    d2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+                }
+                dst[v] = m;
+            }
+            if (want_disp) record_disp(a.disp2, d2);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
 // Batched FP32 Jacobi over a SELL-C-sigma work layout (Kreutzer et al., SIAM J. Sci. Comput. 36(5),
 // 2014): inside every tile the interior vertices are sorted by degree into slices of 32, and a slice's
 // neighbour ids are stored column-major (entry j of slot l at base + 32 j + l, -1 past the slot's row),
@@ -994,6 +1066,18 @@ __global__ void k_pad_rows(int32_t n, const int32_t* __restrict__ row_ptr, const
     const int32_t e0 = row_ptr[v] & 0x7fffffff, e1 = row_ptr[v + 1] & 0x7fffffff;
     const int64_t o0 = 2 * static_cast<int64_t>(pstart[v]), o1 = 2 * static_cast<int64_t>(pstart[v + 1]);
     for (int64_t k = o0; k < o1; ++k) out[k] = e0 + (k - o0) < e1 ? col_idx[e0 + (k - o0)] : -1;
+}
+
+cudaError_t launch_sweep_packed_mesh(const PackedMeshArgs& a, int block, int grid, cudaStream_t stream) {
+    if (a.n_items <= 0) return cudaSuccess;
+    k_sweep_packed_mesh<2><<<grid, block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int sweep_packed_mesh_occupancy(int block) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_packed_mesh<2>, block, 0) != cudaSuccess) return 0;
+    return n;
 }
 
 cudaError_t launch_pad_rows(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* pstart,

@@ -431,6 +431,62 @@ def test_packed_kernel_unavailable_for_a_mesh_of_2_22_id_pairs():
         assert b.autotune()["kernel"] != lms.KERNEL_PACKED
 
 
+def wheel_mesh(spokes=80):
+    """A hub joined to a ring of `spokes` interior vertices inside a fixed outer ring (a fan of triangles
+    around the hub, a triangulated annulus around the fan): the hub's row has `spokes` entries."""
+    t = 2 * np.pi * np.arange(spokes) / spokes
+    xy = np.concatenate([[[0.05, -0.03]], 0.5 * np.c_[np.cos(t), np.sin(t)], np.c_[np.cos(t + 0.1), np.sin(t + 0.1)]])
+    inner, outer = 1 + np.arange(spokes), 1 + spokes + np.arange(spokes)
+    nxt = np.roll(np.arange(spokes), -1)
+    tri = np.concatenate([np.c_[np.zeros(spokes, int), inner, inner[nxt]], np.c_[inner, outer, outer[nxt]],
+                          np.c_[inner, outer[nxt], inner[nxt]]]).astype(np.int32)
+    n = 1 + 2 * spokes
+    adj = [set() for _ in range(n)]
+    for a, b, c in tri:
+        for u, v in ((a, b), (b, c), (c, a)):
+            adj[u].add(int(v))
+            adj[v].add(int(u))
+    row_ptr = np.zeros(n + 1, np.int32)
+    row_ptr[1:] = np.cumsum([len(r) for r in adj])
+    col_idx = np.concatenate([sorted(r) for r in adj]).astype(np.int32)
+    is_boundary = np.zeros(n, np.int8)
+    is_boundary[outer] = 1
+    return dict(n=n, row_ptr=row_ptr, col_idx=col_idx, xy=xy.astype(np.float64), is_boundary=is_boundary, tri=tri)
+
+
+@pytest.mark.parametrize("ordering", [lms.ORI, lms.RDR])
+def test_fp32_jacobi_with_a_row_of_more_than_63_entries(ordering):
+    """The packed single-mesh Jacobi holds a row's length in 6 bits: a mesh with a longer row runs on the
+    row-offset kernel instead, with the same results against the oracle, stop rule included."""
+    m = wheel_mesh(80)
+    assert np.diff(m["row_ptr"]).max() == 80
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 40)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(ordering, seed=3)
+        g.smooth(40)
+        assert err(g.coords(), want, m) <= TOL32
+    _, want_done, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 500, tri=m["tri"],
+                                    tol=1e-4)
+    assert 0 < want_done < 500
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        g.reorder(ordering, seed=3)
+        assert abs(g.smooth(500, lms.JACOBI, 1e-4) - want_done) <= 1
+
+
+def test_fp32_jacobi_across_packed_blocks_and_layouts(mesh_mid):
+    """Packed row words are relative to blocks of 4,096 storage positions (mesh_mid spans three, the last
+    ragged); re-laying the mesh out rebuilds them, and every layout gives the oracle's result."""
+    m = mesh_mid
+    assert m["n"] > 2 * 4096
+    want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], 30)
+    with lms.Mesh.from_dict(m, lms.FP32) as g:
+        for ordering in (lms.RDR, lms.RANDOM, lms.ORI, lms.BRDR):
+            g.set_coords(m["xy"])
+            g.reorder(ordering, seed=11)
+            g.smooth(30)
+            assert err(g.coords(), want, m) <= TOL32, ordering
+
+
 def test_batched_config_rejects_unsupported_chunks():
     with lms.Batch(small_batch(2), ordering=lms.ORI) as b:
         for chunk in (0, 7, 9, -1):
