@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--profile-ordering", choices=[o for o, _ in ORDERINGS],
                     help="profiling driver: the 4096 x 4096 mesh in FP32 under one ordering, 5 Jacobi sweeps "
                          "(run it under ncu to read DRAM bytes and L2 hit rate per ordering); prints no JSON")
+    ap.add_argument("--profile-mode", choices=["jacobi", "gs"], default="jacobi",
+                    help="sweep of --profile-ordering: 5 Jacobi sweeps (one launch each) or 2 coloured-GS sweeps "
+                         "(one launch per colour)")
     return ap.parse_args()
 
 
@@ -914,17 +917,20 @@ def run_reference(args, dist):
     }))
 
 
-def profile_ordering(name):
-    """5 FP32 Jacobi sweeps (single-mesh work-queue kernel) of the 4096 x 4096 mesh under one ordering."""
+def profile_ordering(name, mode="jacobi"):
+    """FP32 sweeps of the 4096 x 4096 mesh under one ordering: 5 Jacobi sweeps (one launch of the packed-row
+    kernel each) or 2 coloured-GS sweeps (one launch per colour range)."""
     import torch
     import meshgen
     import paper_1606_00803_gb300 as lms
     m = meshgen.workload(4)
+    sweeps, smode = (5, lms.JACOBI) if mode == "jacobi" else (2, lms.COLORED_GS)
     with lms.Mesh.from_dict(m, lms.FP32) as g:
         g.reorder(dict(ORDERINGS)[name], seed=meshgen.BASE_SEED + 7)
-        g.smooth(5)
+        g.smooth(sweeps, smode)
         torch.cuda.synchronize()
-        log("profile-ordering %s: %d vertices, 5 sweeps, %.4f ms device time" % (name, m["n"], g.last_stats()["ms"]))
+        log("profile-ordering %s %s: %d vertices, %d colours, %d sweeps, %.4f ms device time"
+            % (name, mode, m["n"], g.colors()[1], sweeps, g.last_stats()["ms"]))
 
 
 def profile_fp64(workload):
@@ -951,7 +957,7 @@ def main():
     if args.profile_ordering:
         import __graft_entry__
         __graft_entry__.build()
-        profile_ordering(args.profile_ordering)
+        profile_ordering(args.profile_ordering, args.profile_mode)
         return
     if args.impl == "reference":
         rank, world, _ = dist_env()

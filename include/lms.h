@@ -270,7 +270,11 @@ int lms_set_launch(lms_handle h, int32_t kernel, int32_t block, int32_t tile);
 
 /* Tile of LMS_BLOCK_GS sweeps in storage positions (tile >= 1), or 0 to choose it by mesh size (about
    eight tiles per SM, within 128..1024).  The sweep's result depends on the tile
-   (it fixes the order).  lms_get_block_tile returns the tile the next sweep uses.  [host] */
+   (it fixes the order).  Tiles below 65,536 positions run one CTA per tile on the ordering's layout; from
+   65,536 up the mesh moves to a layout sorted by (tile colour, vertex colour, ordering position) and each
+   (tile colour, vertex colour) range is one in-place launch, as coloured GS runs its colours - the same
+   order, so the same results either way.  lms_get_block_tile returns the tile the next sweep uses.
+   [host] */
 int lms_set_block_tile(lms_handle h, int32_t tile);
 
 /* How LMS_BLOCK_GS sweeps read positions.  on = 0 (default): through L1 from global memory.  on = 1: each

@@ -217,6 +217,13 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Storage layouts of a mesh handle: the ordering's own, colour-major (coloured GS), and block-range
+// (the block Gauss-Seidel with tiles of at least kBlockRangeTile positions).
+constexpr int kLayoutOrdering = 0, kLayoutColoured = 1, kLayoutBlockRanges = 2;
+// Block Gauss-Seidel tiles from this size up run on the block-range layout, one range per (tile colour,
+// vertex colour); smaller tiles run one CTA per tile on the ordering layout.
+constexpr int32_t kBlockRangeTile = 65536;
+
 }  // namespace
 
 // ------------------------------------------------------------------ handle
@@ -233,11 +240,14 @@ struct lms_mesh_s {
     // orderings
     std::vector<int32_t> user_perm;     // the ordering (new_to_old)
     std::vector<int32_t> perm;          // current storage layout (new_to_old)
-    bool coloured_layout = false;
+    int gs_layout = kLayoutOrdering;    // storage layout kind (kLayout*)
+    int32_t gs_layout_tile = 0;         // tile of the block-range layout
     bool colours_valid = false;
     std::vector<int32_t> colour;        // by original id
     int32_t ncolours = 0;
-    std::vector<int32_t> colour_ofs;    // colour c occupies storage [ofs[c], ofs[c+1])
+    // in-place range layouts: range r occupies storage [range_ofs[r], range_ofs[r+1]); coloured layout: one
+    // range per colour; block-range layout: one per non-empty (tile colour, vertex colour) pair, in order
+    std::vector<int32_t> range_ofs;
     double cx = 0, cy = 0, scale = 1;   // FP32 normalisation
     // device, original labelling
     int32_t *d_rp0 = nullptr, *d_ci0 = nullptr, *d_tri0 = nullptr, *d_vt_ptr = nullptr, *d_vt_idx = nullptr;
@@ -263,14 +273,14 @@ struct lms_mesh_s {
     int4* d_items4 = nullptr;           // tiles over [0, n), then tiles of each colour range
     int64_t items_cap = 0;
     int32_t n_items_all = 0;
-    std::vector<int32_t> item_col_ofs;  // colour c: tiles [n_items_all + ofs[c], n_items_all + ofs[c+1])
+    std::vector<int32_t> item_col_ofs;  // range r: tiles [n_items_all + ofs[r], n_items_all + ofs[r+1])
     int32_t e_cap = 0;
     int32_t* d_rpf = nullptr;           // row offsets of the current layout with the boundary flag in bit 31
     int32_t* d_order = nullptr;         // FP64: thread -> vertex map of the one-thread-per-vertex sweeps
     int2* d_items2 = nullptr;           // FP32 work-queue tiles over [0, n), then over each colour's range
     int64_t items2_cap = 0;
     int32_t n_items2 = 0;               // tiles over [0, n)
-    std::vector<int32_t> item2_col_ofs; // colour c: tiles [n_items2 + ofs[c], n_items2 + ofs[c+1])
+    std::vector<int32_t> item2_col_ofs; // range r: tiles [n_items2 + ofs[r], n_items2 + ofs[r+1])
     // FP32 packed rows of the current layout (Jacobi, k_sweep_packed_mesh); pk_ok false when a row is too long
     bool pk_ok = false;
     int32_t *d_pk_rw = nullptr, *d_pk_bbase = nullptr;
@@ -504,11 +514,11 @@ int build_items(lms_mesh_s* h) {
     add(0, h->n);
     h->n_items_all = int32_t(items.size());
     h->item_col_ofs.assign(1, 0);
-    if (h->coloured_layout)
-        for (int32_t c = 0; c < h->ncolours; ++c) {
-            add(h->colour_ofs[c], h->colour_ofs[c + 1]);
-            h->item_col_ofs.push_back(int32_t(items.size()) - h->n_items_all);
-        }
+    const int32_t nranges = h->gs_layout == kLayoutOrdering ? 0 : int32_t(h->range_ofs.size()) - 1;
+    for (int32_t r = 0; r < nranges; ++r) {
+        add(h->range_ofs[r], h->range_ofs[r + 1]);
+        h->item_col_ofs.push_back(int32_t(items.size()) - h->n_items_all);
+    }
     if (int64_t(items.size()) > h->items_cap) {
         const int64_t cap = int64_t(items.size()) + 64;
         LMS_TRY(h->arena.get(&h->d_items4, cap));
@@ -529,12 +539,11 @@ int build_items(lms_mesh_s* h) {
     for (int32_t v = 0; v < h->n; v += kQueueTile) items2.push_back(make_int2(v, std::min(h->n, v + kQueueTile)));
     const int32_t n_all2 = int32_t(items2.size());
     h->item2_col_ofs.assign(1, 0);
-    if (h->coloured_layout)
-        for (int32_t c = 0; c < h->ncolours; ++c) {
-            for (int32_t v = h->colour_ofs[c]; v < h->colour_ofs[c + 1]; v += kColourTile)
-                items2.push_back(make_int2(v, std::min(h->colour_ofs[c + 1], v + kColourTile)));
-            h->item2_col_ofs.push_back(int32_t(items2.size()) - n_all2);
-        }
+    for (int32_t r = 0; r < nranges; ++r) {
+        for (int32_t v = h->range_ofs[r]; v < h->range_ofs[r + 1]; v += kColourTile)
+            items2.push_back(make_int2(v, std::min(h->range_ofs[r + 1], v + kColourTile)));
+        h->item2_col_ofs.push_back(int32_t(items2.size()) - n_all2);
+    }
     if (int64_t(items2.size()) > h->items2_cap) {
         const int64_t cap = int64_t(items2.size()) + 16;
         LMS_TRY(h->arena.get(&h->d_items2, cap));
@@ -547,7 +556,7 @@ int build_items(lms_mesh_s* h) {
                              h->stream));
     LMS_TRY(check_launch(lms::launch_flag_boundary_rows(h->n, h->d_bits, h->d_rpf, h->stream), "flag_rows"));
     // FP64 one-thread-per-vertex sweeps: inside windows of kOrderWindow storage positions (never crossing
-    // a colour range), threads take the interior vertices by decreasing degree, then the boundary ones, so
+    // a range of an in-place layout), threads take the interior vertices by decreasing degree, then the boundary ones, so
     // the lanes of a warp run rows of one length (the FP64 pipe issues a warp's add for every lane, idle
     // or not).  Each vertex's arithmetic is unchanged, so results are too.
     std::vector<int32_t> order;
@@ -555,7 +564,7 @@ int build_items(lms_mesh_s* h) {
         constexpr int32_t kOrderWindow = 1024;
         order.resize(h->n);
         std::vector<int32_t> cuts{0, h->n};
-        if (h->coloured_layout) cuts.insert(cuts.end() - 1, h->colour_ofs.begin() + 1, h->colour_ofs.end());
+        if (nranges > 0) cuts.insert(cuts.end() - 1, h->range_ofs.begin() + 1, h->range_ofs.end());
         std::sort(cuts.begin(), cuts.end());
         cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
         std::vector<int32_t> count;
@@ -590,9 +599,15 @@ int ensure_queue(lms_mesh_s* h, int32_t slots) {
     return LMS_OK;
 }
 
-int launches_per_sweep(lms_mesh_s* h, int mode) {
-    if (mode == LMS_BLOCK_GS) return std::max<int>(1, int(h->block_tc_ofs.size()) - 1);
-    return mode == LMS_COLORED_GS ? h->ncolours : 1;
+// The block Gauss-Seidel on the block-range layout (tiles of kBlockRangeTile positions or more).
+int32_t block_tile_for(const lms_mesh_s* h);
+bool block_range_form(const lms_mesh_s* h) { return block_tile_for(h) >= kBlockRangeTile; }
+
+// Work-queue counters one sweep uses: one per launch.
+int queue_slots_per_sweep(lms_mesh_s* h, int mode) {
+    if (mode == LMS_BLOCK_GS && !block_range_form(h)) return std::max<int>(1, int(h->block_tc_ofs.size()) - 1);
+    if (mode == LMS_COLORED_GS || mode == LMS_BLOCK_GS) return std::max<int>(1, int(h->range_ofs.size()) - 1);
+    return 1;
 }
 
 // FP32 Jacobi and coloured GS with the direct kernel run on the work-queue sweep (rows in chunks of 4).
@@ -622,7 +637,8 @@ int ensure_colours(lms_mesh_s* h) {
 
 // Tile of the block Gauss-Seidel: the requested one, else about eight tiles per SM, at most 1,024
 // positions (on the 18.4M-vertex mesh larger tiles were slower: 0.66 / 0.75 / 0.80 ms per FP32 sweep
-// at 1,024 / 2,048 / 4,096).
+// at 1,024 / 2,048 / 4,096).  From kBlockRangeTile up the sweep runs on the block-range layout (RDR,
+// FP32: 0.99 / 0.66 / 0.54 / 0.46 ms per sweep at 2^20 / 2^21 / 2^22 / 2^23 positions; coloured GS 0.39).
 int32_t block_tile_for(const lms_mesh_s* h) {
     if (h->block_tile_req > 0) return h->block_tile_req;
     const int64_t want = int64_t(h->n) / (int64_t(h->sms) * 8);
@@ -699,36 +715,66 @@ int ensure_block_tables(lms_mesh_s* h) {
     return LMS_OK;
 }
 
-// The ordering's own layout (after a coloured Gauss-Seidel moved the mesh to the colour-major one).
+// The ordering's own layout (after an in-place sweep moved the mesh to a range layout).
 int ensure_ordering_layout(lms_mesh_s* h) {
-    if (!h->coloured_layout) return LMS_OK;
+    if (h->gs_layout == kLayoutOrdering) return LMS_OK;
     LMS_TRY(apply_layout(h, h->user_perm));
-    h->coloured_layout = false;
+    h->gs_layout = kLayoutOrdering;
+    h->range_ofs.clear();
+    return build_items(h);
+}
+
+// Range layout: the interior vertices grouped by key[v] (0 .. nkeys - 1; stable in the ordering's
+// position), one range per non-empty key in ascending key order, then the boundary vertices (key -1).
+int apply_range_layout(lms_mesh_s* h, const std::vector<int32_t>& key_by_pos, int32_t nkeys, int kind) {
+    const int32_t n = h->n;
+    std::vector<int32_t> start(size_t(nkeys) + 1, 0);
+    for (int32_t k = 0; k < n; ++k)
+        if (key_by_pos[k] >= 0) ++start[key_by_pos[k] + 1];
+    for (int32_t c = 0; c < nkeys; ++c) start[c + 1] += start[c];
+    std::vector<int32_t> fill(start.begin(), start.end()), p(n);
+    int32_t tail = start[nkeys];
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t c = key_by_pos[k];
+        p[c >= 0 ? fill[c]++ : tail++] = h->user_perm[k];
+    }
+    h->range_ofs.assign(1, 0);
+    for (int32_t c = 0; c < nkeys; ++c)
+        if (start[c + 1] > start[c]) h->range_ofs.push_back(start[c + 1]);
+    LMS_TRY(apply_layout(h, p));
+    h->gs_layout = kind;
     return build_items(h);
 }
 
 int ensure_coloured_layout(lms_mesh_s* h) {
-    if (h->coloured_layout) return LMS_OK;
+    if (h->gs_layout == kLayoutColoured) return LMS_OK;
     LMS_TRY(ensure_colours(h));
-    const int32_t n = h->n, nc = h->ncolours;
-    h->colour_ofs.assign(nc + 1, 0);
-    for (int32_t v = 0; v < n; ++v)
-        if (h->colour[v] >= 0) h->colour_ofs[h->colour[v] + 1]++;
-    for (int32_t c = 0; c < nc; ++c) h->colour_ofs[c + 1] += h->colour_ofs[c];
-    std::vector<int32_t> fill(h->colour_ofs.begin(), h->colour_ofs.end());
-    std::vector<int32_t> p(n);
-    int32_t tail = h->colour_ofs[nc];
-    for (int32_t k = 0; k < n; ++k) {  // stable in the ordering's position
-        int32_t v = h->user_perm[k];
-        int32_t c = h->colour[v];
-        if (c >= 0)
-            p[fill[c]++] = v;
-        else
-            p[tail++] = v;
+    std::vector<int32_t> key(h->n);
+    for (int32_t k = 0; k < h->n; ++k) key[k] = h->colour[h->user_perm[k]];
+    return apply_range_layout(h, key, h->ncolours, kLayoutColoured);
+}
+
+// Block-range layout of the block Gauss-Seidel with tile `tile`: interior vertices by (tile colour, vertex
+// colour, ordering position).  Tiles of one tile colour share no edge between interior vertices and a
+// colour's vertices inside a tile are independent, so sweeping the ranges one after another, each range
+// in one step, is the in-place sweep in lms_block_order's (tile colour, tile, vertex colour, position)
+// order.
+int ensure_block_range_layout(lms_mesh_s* h, int32_t tile) {
+    if (h->gs_layout == kLayoutBlockRanges && h->gs_layout_tile == tile) return LMS_OK;
+    LMS_TRY(ensure_colours(h));
+    const int32_t n = h->n;
+    const int64_t ntiles = (int64_t(n) + tile - 1) / tile;
+    std::vector<int32_t> tile_colour(static_cast<size_t>(ntiles)), order(n), key(n);
+    int32_t ntc = 0, n_order = 0;
+    LMS_TRY(lms::block_order(n, h->rp.data(), h->ci.data(), h->bnd.data(), h->user_perm.data(), tile,
+                             tile_colour.data(), &ntc, order.data(), &n_order));
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t c = h->colour[h->user_perm[k]];
+        key[k] = c < 0 ? -1 : tile_colour[k / tile] * h->ncolours + c;
     }
-    LMS_TRY(apply_layout(h, p));
-    h->coloured_layout = true;
-    return build_items(h);
+    LMS_TRY(apply_range_layout(h, key, ntc * h->ncolours, kLayoutBlockRanges));
+    h->gs_layout_tile = tile;
+    return LMS_OK;
 }
 
 SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
@@ -749,6 +795,9 @@ SweepArgs sweep_args(lms_mesh_s* h, int src, int dst) {
 // base = buffer holding sweep 0.  Jacobi: reads buf[(base + k1 - 1) & 1], writes the other.
 int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stoppable, cudaStream_t s) {
     const int src = (base + k1 - 1) & 1;
+    // on the block-range layout the block Gauss-Seidel sweeps its ranges exactly as coloured GS does
+    if (mode == LMS_BLOCK_GS && h->gs_layout == kLayoutBlockRanges) mode = LMS_COLORED_GS;
+    const int32_t nranges = h->gs_layout == kLayoutOrdering ? 0 : int32_t(h->range_ofs.size()) - 1;
     if (mode == LMS_BLOCK_GS && h->block_staged && h->st_valid) {  // one launch per tile colour, staged
         lms::BlockGsStagedArgs a{};
         a.xy = h->d_xy[base];
@@ -811,7 +860,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
         const int occ = std::max(1, lms::staged_occupancy(h->precision, mode != LMS_JACOBI, h->block, h->tile, h->e_cap));
-        const int ranges = mode == LMS_JACOBI ? 1 : h->ncolours;
+        const int ranges = mode == LMS_JACOBI ? 1 : nranges;
         for (int32_t c = 0; c < ranges; ++c) {
             if (mode == LMS_JACOBI) {
                 a.bnd_bits = h->d_bits;
@@ -820,7 +869,7 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
                 a.items = h->d_items4;
                 a.n_items = h->n_items_all;
             } else {
-                a.bnd_bits = nullptr;  // every vertex of a colour range is interior
+                a.bnd_bits = nullptr;  // every vertex of a range is interior
                 a.src = h->d_xy[base];
                 a.dst = h->d_xy[base];
                 a.items = h->d_items4 + h->n_items_all + h->item_col_ofs[c];
@@ -859,10 +908,10 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
     if (uses_queue_sweep(h, mode)) {
         constexpr int kChunk = 4, kBlock = 128;
         const int occ = std::max(1, lms::batch_sweep_occupancy(kBlock, kChunk));
-        // Jacobi: one launch over [0, n) from one buffer into the other.  Coloured GS: one launch per
-        // colour range, in place - a colour's vertices are never neighbours of one another, so no launch
-        // reads a position it writes.
-        const int ranges = mode == LMS_JACOBI ? 1 : h->ncolours;
+        // Jacobi: one launch over [0, n) from one buffer into the other.  In-place sweeps: one launch per
+        // range, in place - a range's vertices are never neighbours of one another, so no launch reads a
+        // position it writes.
+        const int ranges = mode == LMS_JACOBI ? 1 : nranges;
         for (int32_t c = 0; c < ranges; ++c) {
             SweepArgs a = mode == LMS_JACOBI ? sweep_args(h, src, src ^ 1) : sweep_args(h, base, base);
             a.row_ptr = h->d_rpf;
@@ -889,12 +938,12 @@ int issue_sweep(lms_mesh_s* h, int mode, int base, int k1, bool disp, bool stopp
         a.order = h->precision == LMS_FP64 ? h->d_order : nullptr;
         return check_launch(lms::launch_sweep(h->precision, false, a, h->block, h->fp64_arith, s), "sweep");
     }
-    for (int32_t c = 0; c < h->ncolours; ++c) {
+    for (int32_t c = 0; c < nranges; ++c) {
         SweepArgs a = sweep_args(h, base, base);
         a.order = h->precision == LMS_FP64 ? h->d_order : nullptr;
-        a.bnd_bits = nullptr;  // every vertex of a colour range is interior
-        a.v_begin = h->colour_ofs[c];
-        a.v_end = h->colour_ofs[c + 1];
+        a.bnd_bits = nullptr;  // every vertex of a range is interior
+        a.v_begin = h->range_ofs[c];
+        a.v_end = h->range_ofs[c + 1];
         a.state = stoppable ? h->d_state : nullptr;
         a.disp2 = disp ? &h->d_state->disp2[k1 & 1] : nullptr;
         LMS_TRY(check_launch(lms::launch_sweep(h->precision, true, a, h->block, h->fp64_arith, s), "sweep"));
@@ -1107,7 +1156,8 @@ int lms_reorder(lms_handle h, int ordering, uint64_t seed) {
     h->user_perm = p;
     h->colours_valid = false;
     h->block_valid = false;
-    h->coloured_layout = false;
+    h->gs_layout = kLayoutOrdering;
+    h->range_ofs.clear();
     LMS_TRY(apply_layout(h, p));
     LMS_TRY(build_items(h));
     LMS_CUDA(cudaStreamSynchronize(h->stream));
@@ -1198,8 +1248,12 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
     if (tol >= 0.0 && h->ntri == 0) return LMS_ERR_NO_TRIANGLES;
     LMS_TRY(finish_stats(h));
     if (mode == LMS_COLORED_GS) LMS_TRY(ensure_coloured_layout(h));
-    if (mode == LMS_INPLACE_STATIC || mode == LMS_BLOCK_GS) LMS_TRY(ensure_ordering_layout(h));
-    if (mode == LMS_BLOCK_GS) LMS_TRY(ensure_block_tables(h));
+    if (mode == LMS_BLOCK_GS && block_range_form(h)) {
+        LMS_TRY(ensure_block_range_layout(h, block_tile_for(h)));
+    } else if (mode == LMS_INPLACE_STATIC || mode == LMS_BLOCK_GS) {
+        LMS_TRY(ensure_ordering_layout(h));
+        if (mode == LMS_BLOCK_GS) LMS_TRY(ensure_block_tables(h));
+    }
     if (iters_done) *iters_done = 0;
     h->q_first = h->q_last = NAN;
     h->last_disp = NAN;
@@ -1213,7 +1267,7 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
         key += "/" + std::to_string(h->kernel) + "/" + std::to_string(h->block) + "/" + std::to_string(h->tile);
         cudaGraphExec_t exec;
         int64_t kernels = 0;
-        const int32_t slots = max_iters * launches_per_sweep(h, mode);
+        const int32_t slots = max_iters * queue_slots_per_sweep(h, mode);
         LMS_TRY(ensure_queue(h, slots));
         LMS_TRY(get_graph(h, key,
                           [&](cudaStream_t cs) -> int {
@@ -1256,7 +1310,7 @@ int lms_smooth(lms_handle h, int32_t max_iters, int mode, double tol, int32_t* i
                       std::to_string(h->tile);
     cudaGraphExec_t exec;
     int64_t kernels = 0;
-    const int32_t slots = kChunk * launches_per_sweep(h, mode);
+    const int32_t slots = kChunk * queue_slots_per_sweep(h, mode);
     LMS_TRY(ensure_queue(h, slots));
     LMS_TRY(get_graph(h, key,
                       [&](cudaStream_t cs) -> int {
