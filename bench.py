@@ -545,7 +545,7 @@ def batched_per_ordering(meshes, cfg, hbm_peak, ab, wants):
                          "after %d sweeps" % (cfg, SWEEPS_PER_STEP), rows=rows)
 
 
-def fp64_plain_table(hbm_peak):
+def fp64_plain_table(hbm_peak, m=None):
     """FP64 plain form beside the FP32 batched headline: the 4096 x 4096 mesh (~18.4M vertices, positions
     larger than L2) in the RDR ordering, Jacobi, 20-sweep graphs, FP64 and FP32; each result after 20 sweeps
     compared with the FP64 oracle."""
@@ -554,7 +554,7 @@ def fp64_plain_table(hbm_peak):
     import oracle
     import paper_1606_00803_gb300 as lms
     sweeps = 20
-    m = meshgen.workload(4)
+    m = meshgen.workload(4) if m is None else m
     n, nnz = m["n"], m["nnz"]
     n_int = int((m["is_boundary"] == 0).sum())
     want, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m["xy"], sweeps)
@@ -585,6 +585,52 @@ def fp64_plain_table(hbm_peak):
                          "Jacobi, %d-sweep graphs; algorithmic bytes per sweep FP64 %.0f MB, FP32 %.0f MB" %
                          (n, n_int, sweeps, algorithmic_bytes_fp64(n, n_int, nnz) / 1e6,
                           algorithmic_bytes_fp32(n, n_int, nnz) / 1e6), rows=rows)
+
+
+def inplace_table(hbm_peak, m):
+    """In-place sweeps of the 4096 x 4096 mesh in the RDR ordering, FP32: coloured GS, the block Gauss-Seidel
+    with 2^23-position tiles (block-range layout: one in-place launch per (tile colour, vertex colour)
+    range) and with the tile chosen by mesh size (one CTA per tile).  Per sweep: time (20-sweep graphs) and
+    algorithmic bytes; sweeps until the mean quality gains less than 1e-6 in a sweep; FP32 error after 20
+    sweeps against the FP64 device sweeps in the same order (tests hold those equal to the oracle's bit for
+    bit; the oracle itself needs ~40 s per 20 sweeps at this size)."""
+    import math
+    import numpy as np
+    import torch
+    import meshgen
+    import paper_1606_00803_gb300 as lms
+    sweeps = 20
+    n, nnz = m["n"], m["nnz"]
+    n_int = int((m["is_boundary"] == 0).sum())
+    diag = math.hypot(np.ptp(m["xy"][:, 0]), np.ptp(m["xy"][:, 1]))
+    ab = algorithmic_bytes_fp32(n, n_int, nnz)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    with lms.Mesh.from_dict(m, lms.FP32) as g32, lms.Mesh.from_dict(m, lms.FP64) as g64:
+        for g in (g32, g64):
+            g.reorder(lms.RDR, seed=meshgen.BASE_SEED + 7)
+        for name, mode, tile in (("coloured_gs", lms.COLORED_GS, 0), ("block_gs_tile_2^23", lms.BLOCK_GS, 1 << 23),
+                                 ("block_gs_tile_by_size", lms.BLOCK_GS, 0)):
+            for g in (g32, g64):
+                g.set_block_tile(tile)
+            g32.set_coords(m["xy"])
+            g32.smooth(sweeps, mode=mode)
+            torch.cuda.synchronize()
+            ms = min(time_graph(lambda: g32.smooth(sweeps, mode=mode), stream, 1) for _ in range(3)) / sweeps
+            g32.set_coords(m["xy"])
+            g32.smooth(sweeps, mode=mode)
+            g64.set_coords(m["xy"])
+            g64.smooth(sweeps, mode=mode)
+            err = float(np.abs(g32.coords() - g64.coords()).max() / diag)
+            g32.set_coords(m["xy"])
+            k = g32.smooth(1000, mode=mode, tol=1e-6)
+            gbs = ab / (ms * 1e-3) / 1e9
+            rows[name] = dict(tile=g32.block_tile() if mode == lms.BLOCK_GS else None, sweep_ms=round(ms, 4),
+                              updates_per_s=n_int / (ms * 1e-3), algorithmic_gbs=round(gbs, 1),
+                              hbm_frac=round(gbs / hbm_peak, 3), sweeps_to_rule=k,
+                              err_fp32_vs_fp64_over_diag=err)
+    return dict(workload="4096 x 4096 mesh (%d vertices), RDR, FP32; algorithmic bytes per sweep %.0f MB (Jacobi's); "
+                         "rule: mean quality gain < 1e-6" % (n, ab / 1e6), rows=rows)
 
 
 def large_table(hbm_peak):
@@ -750,7 +796,11 @@ def run_ours(args, dist):
     extras = {}
     if extras_wanted:
         extras["per_ordering"] = per_ordering_table(hbm_peak)
-        extras["fp64_plain"] = fp64_plain_table(hbm_peak)
+        import meshgen
+        m4 = meshgen.workload(4)
+        extras["fp64_plain"] = fp64_plain_table(hbm_peak, m4)
+        extras["inplace_w4"] = inplace_table(hbm_peak, m4)
+        del m4
         extras["stopping_rule"] = stopping_table(finish_oracle_stop_sweeps(stop_pool))
         if args.full:
             extras["large"] = large_table(hbm_peak)
