@@ -98,83 +98,142 @@ void order_bfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_
     }
 }
 
-// Interior vertices in increasing (quality, id): a stable LSD radix sort (16-bit digits) of the
-// qualities' bit patterns, which order like the values for non-negative doubles; the input is in
-// ascending id, so equal qualities stay in ascending id.
+// Threads for `count` items: up to 16 (and the host's), fewer when a thread would get fewer than
+// min_per_thread items.
+int64_t parts_for(int64_t count, int64_t min_per_thread) {
+    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    return std::max<int64_t>(1, std::min<int64_t>({16, hw, count / std::max<int64_t>(1, min_per_thread)}));
+}
+
+// Runs f(t, nt, lo, hi) for t = 0 .. nt - 1 (nt = parts_for(count, min_per_thread)) over [0, count) cut
+// into nt equal parts, part 0 on the calling thread.
+template <typename F>
+void parallel_parts(int64_t count, int64_t min_per_thread, F&& f) {
+    const int64_t nt = parts_for(count, min_per_thread);
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < nt; ++t)
+        pool.emplace_back([&f, count, nt, t] { f(t, nt, count * t / nt, count * (t + 1) / nt); });
+    f(0, nt, 0, count / nt);
+    for (auto& th : pool) th.join();
+}
+
+// ids (ascending on entry) in increasing (quality, id): a stable LSD radix sort (16-bit digits) of the
+// qualities' bit patterns, which order like the values for non-negative doubles, so equal qualities stay
+// in ascending id.  Each pass counts digits per thread part, turns the counts into per-(digit, part)
+// offsets and scatters each part in order, which keeps the sort stable.
 void sort_by_quality(std::vector<int32_t>& ids, const double* q) {
     const size_t m = ids.size();
     std::vector<uint64_t> key(m), key2(m);
     std::vector<int32_t> ids2(m);
-    for (size_t i = 0; i < m; ++i) {
-        const double x = q[ids[i]] == 0.0 ? 0.0 : q[ids[i]];  // -0.0 sorts with +0.0
-        std::memcpy(&key[i], &x, sizeof(double));
-    }
-    std::vector<size_t> count(65537);
+    parallel_parts(int64_t(m), 1 << 16, [&](int64_t, int64_t, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const double x = q[ids[i]] == 0.0 ? 0.0 : q[ids[i]];  // -0.0 sorts with +0.0
+            std::memcpy(&key[i], &x, sizeof(double));
+        }
+    });
+    constexpr size_t kDigits = 65536;
+    std::vector<size_t> count;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 16 * pass;
-        std::fill(count.begin(), count.end(), 0);
-        for (size_t i = 0; i < m; ++i) count[((key[i] >> shift) & 0xffff) + 1]++;
-        if (count[(key[0] >> shift & 0xffff) + 1] == m) continue;  // one digit value only: already ordered
-        for (size_t d = 0; d < 65536; ++d) count[d + 1] += count[d];
-        for (size_t i = 0; i < m; ++i) {
-            const size_t at = count[(key[i] >> shift) & 0xffff]++;
-            key2[at] = key[i];
-            ids2[at] = ids[i];
-        }
+        bool one_digit = true;  // one digit value only: already ordered
+        const uint64_t d0 = (key[0] >> shift) & 0xffff;
+        for (size_t i = 0; i < m && one_digit; ++i) one_digit = ((key[i] >> shift) & 0xffff) == d0;
+        if (one_digit) continue;
+        const int64_t parts = parts_for(int64_t(m), 1 << 16);
+        count.assign(size_t(parts) * kDigits, 0);
+        // count[t * kDigits + d]: keys of part t with digit d, then the offset of the first of them
+        parallel_parts(int64_t(m), 1 << 16, [&](int64_t t, int64_t, int64_t lo, int64_t hi) {
+            size_t* c = count.data() + size_t(t) * kDigits;
+            for (int64_t i = lo; i < hi; ++i) ++c[(key[i] >> shift) & 0xffff];
+        });
+        size_t at = 0;
+        for (size_t d = 0; d < kDigits; ++d)
+            for (int64_t t = 0; t < parts; ++t) {
+                const size_t c = count[size_t(t) * kDigits + d];
+                count[size_t(t) * kDigits + d] = at;
+                at += c;
+            }
+        parallel_parts(int64_t(m), 1 << 16, [&](int64_t t, int64_t, int64_t lo, int64_t hi) {
+            size_t* c = count.data() + size_t(t) * kDigits;
+            for (int64_t i = lo; i < hi; ++i) {
+                const size_t to = c[(key[i] >> shift) & 0xffff]++;
+                key2[to] = key[i];
+                ids2[to] = ids[i];
+            }
+        });
         key.swap(key2);
         ids.swap(ids2);
     }
 }
 
-// Algorithm 2.  `done` = processed (the walk has expanded the vertex), `placed` = sorted (it has a
-// position in the new order).
+// Algorithm 2.  Every vertex gets its rank in increasing (quality, id) order once; the seeds are the
+// interior vertices in rank order, and every CSR row is sorted by rank once (in parallel), so the walk's
+// list l - the unprocessed neighbours of the current vertex by increasing key - is the current row with
+// the processed members skipped.  `done` = processed (the walk has expanded the vertex), `placed` =
+// sorted (it has a position in the new order).
 void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
                const double* q, int32_t* out) {
-    KeyLess less{q};
-    std::vector<int32_t> seeds;
-    seeds.reserve(n);
-    for (int32_t v = 0; v < n; ++v)
-        if (!is_boundary[v]) seeds.push_back(v);
+    std::vector<int32_t> by_key(n);
+    for (int32_t v = 0; v < n; ++v) by_key[v] = v;
     bool non_negative = true;
-    for (int32_t v : seeds) non_negative = non_negative && q[v] >= 0.0;
-    if (non_negative && !seeds.empty())
-        sort_by_quality(seeds, q);
+    for (int32_t v = 0; v < n; ++v) non_negative = non_negative && q[v] >= 0.0;
+    if (non_negative)
+        sort_by_quality(by_key, q);
     else
-        std::sort(seeds.begin(), seeds.end(), less);
+        std::sort(by_key.begin(), by_key.end(), KeyLess{q});
+    std::vector<int32_t> rank(n);
+    parallel_parts(n, 1 << 16, [&](int64_t, int64_t, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) rank[by_key[i]] = int32_t(i);
+    });
+    std::vector<int32_t> row(col_idx, col_idx + row_ptr[n]);
+    parallel_parts(n, 1 << 16, [&](int64_t, int64_t, int64_t lo, int64_t hi) {  // rows are short: insertion sort
+        for (int64_t v = lo; v < hi; ++v)
+            for (int32_t e = row_ptr[v] + 1; e < row_ptr[v + 1]; ++e)
+                for (int32_t k = e; k > row_ptr[v] && rank[row[k]] < rank[row[k - 1]]; --k) std::swap(row[k], row[k - 1]);
+    });
 
-    std::vector<uint8_t> done(n, 0), placed(n, 0);
-    std::vector<int32_t> l;
+    // the walk moves between neighbours, so it runs over vertex ids (nearby in memory); the seeds are
+    // scanned in rank order over a bitmap by rank of the vertices that are boundary or processed
+    constexpr uint8_t kDone = 1, kPlaced = 2;
+    std::vector<uint8_t> state(n, 0);
+    std::vector<uint64_t> skip((size_t(n) + 63) / 64, 0);
+    for (int32_t v = 0; v < n; ++v)
+        if (is_boundary[v]) skip[size_t(rank[v]) >> 6] |= uint64_t(1) << (rank[v] & 63);
     int32_t pos = 0;
     auto place = [&](int32_t v) {
-        if (!placed[v]) {
-            placed[v] = 1;
+        if (!(state[v] & kPlaced)) {
+            state[v] |= kPlaced;
             out[pos++] = v;
         }
     };
-    // l <- unprocessed neighbours of v by increasing key (rows are short: insertion sort)
-    auto gather = [&](int32_t v) {
-        l.clear();
-        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-            int32_t u = col_idx[e];
-            if (done[u]) continue;
-            l.push_back(u);
-            for (size_t k = l.size() - 1; k > 0 && less(l[k], l[k - 1]); --k) std::swap(l[k], l[k - 1]);
-        }
+    auto process = [&](int32_t v) {
+        state[v] |= kDone;
+        skip[size_t(rank[v]) >> 6] |= uint64_t(1) << (rank[v] & 63);
     };
-    for (int32_t s : seeds) {
-        if (done[s]) continue;
-        place(s);
-        done[s] = 1;
-        gather(s);
-        while (!l.empty()) {
-            for (int32_t u : l) place(u);
-            int32_t w = l.front();
-            done[w] = 1;
-            gather(w);
+    for (size_t w = 0; w < skip.size(); ++w) {
+        for (uint64_t free = ~skip[w]; free != 0; free = ~skip[w]) {
+            const int64_t i = int64_t(w) * 64 + __builtin_ctzll(free);
+            if (i >= n) break;
+            const int32_t s = by_key[i];  // the worst interior vertex not yet processed
+            place(s);
+            process(s);
+            for (int32_t cur = s;;) {
+                int32_t next = -1;  // l[0]
+                for (int32_t e = row_ptr[cur]; e < row_ptr[cur + 1]; ++e) {
+                    const int32_t u = row[e];
+                    if (state[u] & kDone) continue;
+                    if (next < 0) next = u;
+                    place(u);
+                }
+                if (next < 0) break;
+                process(next);
+                cur = next;
+            }
         }
     }
     for (int32_t v = 0; v < n; ++v) place(v);  // vertices no walk reached, ascending id
 }
+
 // Block RDR (a data-parallel variant of Algorithm 2; not in the paper): the BFS order `bfs` cut into
 // blocks of `block` consecutive positions, Algorithm 2 run on each block's own subgraph (walks only
 // through vertices of the block; members no walk reached follow in ascending id), blocks kept in BFS

@@ -96,6 +96,26 @@ def test_host_ordering_matches_oracle(side, ordering):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("ordering", [lms.RDR, lms.BRDR])
+def test_host_rdr_on_several_threads_matches_oracle(ordering):
+    """From 131,072 vertices up the host RDR sorts the keys, ranks the vertices and orders the rows on
+    several threads; the walk is the same."""
+    m = meshgen.workload(1, side=400)
+    assert m["n"] > 2 * 65536
+    q = oracle.vertex_quality(m["n"], m["tri"], m["xy"])
+    assert np.array_equal(lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], ordering, q_v=q),
+                          oracle.order(m, ordering, q_v=q))
+
+
+def test_host_rdr_with_negative_keys_matches_oracle():
+    """Keys below zero take the comparison sort instead of the radix sort of the bit patterns."""
+    m = meshgen.workload(1, side=60)
+    q = np.random.default_rng(4).uniform(-1.0, 1.0, m["n"])
+    q[::7] = -0.0
+    assert np.array_equal(lms.order_host(m["row_ptr"], m["col_idx"], m["is_boundary"], lms.RDR, q_v=q),
+                          oracle.order_rdr(m["row_ptr"], m["col_idx"], m["is_boundary"], q))
+
+
 def test_host_rdr_handles_ties_and_unreached_vertices():
     import json
     from conftest import GOLDEN
