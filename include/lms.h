@@ -205,7 +205,9 @@ int lms_block_order(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, c
  * Diagnostic of the LMS_BLOCK_GS tables: builds them for storage order new_to_old and tile as a handle
  * does, and walks them in the device sweep's launch order (tile colour, tile, colour group, table
  * order), writing the visited interior vertices (original ids) to seq ([n]), their count to *nseq and
- * the number of launches of one sweep to *n_launches.  Equals lms_block_order's order.  LMS_ERR_ARG,
+ * the number of launches of one sweep to *n_launches (the one-CTA-per-tile form of tiles below 65,536
+ * positions: one launch per tile colour; tiles from 65,536 up run one launch per non-empty (tile colour,
+ * vertex colour) range instead, in the same order).  Equals lms_block_order's order.  LMS_ERR_ARG,
  * LMS_ERR_OOM.  [host]
  */
 int lms_block_walk(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const uint8_t* is_boundary,
