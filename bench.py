@@ -34,7 +34,7 @@ METRIC = "vertex updates/s and % HBM roofline: FP32 batched vs FP64 plain, per o
 UNIT = "vertex updates/s"
 SWEEPS_PER_STEP = 50
 PER_ORDERING_SWEEPS = 100
-E2E_GROUPS = 4  # mesh groups of the pipelined end-to-end call (sizes 1 : 4 : 4 : 1)
+E2E_GROUPS = 6  # mesh groups of the pipelined end-to-end call (sizes 1 : 4 : 16 : 16 : 4 : 1)
 ORDERINGS = (("ori", 0), ("random", 1), ("bfs", 2), ("rdr", 3), ("rbfs", 4), ("brdr", 5))  # LMS_ORI .. LMS_BRDR
 L2_BYTES = 129 * 2 ** 20
 FP64_OPS_PEAK_NOTE = ("the FP64 unit's rate, 2 instructions/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s "
