@@ -236,3 +236,22 @@ def test_block_gs_range_form_stopping_rule_and_mixed_modes():
     m2["xy"], _, _ = oracle.block_gs_smooth(m2, p, 500, 2)
     x, _, _ = oracle.smooth(m["row_ptr"], m["col_idx"], m["is_boundary"], m2["xy"], 1)
     assert np.array_equal(chained, x)
+
+
+@pytest.mark.parametrize("precision", [lms.FP64, lms.FP32])
+def test_block_gs_range_form_with_the_staged_kernel(mesh_big, precision):
+    """The staged kernel (TMA tiles of rows and ids) sweeps the block-range layout's ranges too: FP64
+    bit-exact, FP32 within tolerance."""
+    m = mesh_big
+    p = oracle.order(m, oracle.RDR)
+    want, _, _ = oracle.block_gs_smooth(m, p, RANGE_TILE, 4)
+    with lms.Mesh.from_dict(m, precision) as g:
+        g.reorder(lms.RDR)
+        g.set_launch(lms.KERNEL_STAGED, 256, 256)
+        g.set_block_tile(RANGE_TILE)
+        g.smooth(4, mode=lms.BLOCK_GS)
+        got = g.coords()
+    if precision == lms.FP64:
+        assert np.array_equal(got, want)
+    else:
+        assert np.abs(got - want).max() <= TOL32 * diag(m)
