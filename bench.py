@@ -57,9 +57,10 @@ def parse_args():
     ap.add_argument("--profile-ordering", choices=[o for o, _ in ORDERINGS],
                     help="profiling driver: the 4096 x 4096 mesh in FP32 under one ordering, 5 Jacobi sweeps "
                          "(run it under ncu to read DRAM bytes and L2 hit rate per ordering); prints no JSON")
-    ap.add_argument("--profile-mode", choices=["jacobi", "gs"], default="jacobi",
-                    help="sweep of --profile-ordering: 5 Jacobi sweeps (one launch each) or 2 coloured-GS sweeps "
-                         "(one launch per colour)")
+    ap.add_argument("--profile-mode", choices=["jacobi", "gs", "bgs"], default="jacobi",
+                    help="sweep of --profile-ordering: 5 Jacobi sweeps (one launch each), 2 coloured-GS sweeps "
+                         "(one launch per colour) or 2 block Gauss-Seidel sweeps with 2^23-position tiles (one "
+                         "launch per tile colour and vertex colour)")
     return ap.parse_args()
 
 
@@ -975,13 +976,15 @@ def profile_ordering(name, mode="jacobi"):
     import meshgen
     import paper_1606_00803_gb300 as lms
     m = meshgen.workload(4)
-    sweeps, smode = (5, lms.JACOBI) if mode == "jacobi" else (2, lms.COLORED_GS)
+    sweeps, smode = {"jacobi": (5, lms.JACOBI), "gs": (2, lms.COLORED_GS), "bgs": (2, lms.BLOCK_GS)}[mode]
     with lms.Mesh.from_dict(m, lms.FP32) as g:
         g.reorder(dict(ORDERINGS)[name], seed=meshgen.BASE_SEED + 7)
+        if mode == "bgs":
+            g.set_block_tile(1 << 23)
         g.smooth(sweeps, smode)
         torch.cuda.synchronize()
-        log("profile-ordering %s %s: %d vertices, %d colours, %d sweeps, %.4f ms device time"
-            % (name, mode, m["n"], g.colors()[1], sweeps, g.last_stats()["ms"]))
+        log("profile-ordering %s %s: %d vertices, %d colours, %d sweeps, %d launches, %.4f ms device time"
+            % (name, mode, m["n"], g.colors()[1], sweeps, g.last_launches(), g.last_stats()["ms"]))
 
 
 def profile_fp64(workload):
