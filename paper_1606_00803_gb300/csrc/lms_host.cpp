@@ -217,12 +217,27 @@ void order_rdr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const 
             const int32_t s = by_key[i];  // the worst interior vertex not yet processed
             place(s);
             process(s);
+            // the next seed is usually far from this walk: start loading its row now
+            for (size_t x = w, k = 0; x < skip.size() && k < 4; ++x, ++k) {
+                const uint64_t ahead = ~skip[x] & (x == w ? ~uint64_t(0) << 1 << (i & 63) : ~uint64_t(0));
+                if (ahead == 0) continue;
+                const int64_t j = int64_t(x) * 64 + __builtin_ctzll(ahead);
+                if (j < n) {
+                    __builtin_prefetch(row_ptr + by_key[j]);
+                    __builtin_prefetch(row.data() + row_ptr[by_key[j]]);
+                }
+                break;
+            }
             for (int32_t cur = s;;) {
                 int32_t next = -1;  // l[0]
                 for (int32_t e = row_ptr[cur]; e < row_ptr[cur + 1]; ++e) {
                     const int32_t u = row[e];
                     if (state[u] & kDone) continue;
-                    if (next < 0) next = u;
+                    if (next < 0) {  // l[0] is known: start loading its row while the rest of l is placed
+                        next = u;
+                        __builtin_prefetch(row_ptr + u);
+                        __builtin_prefetch(row.data() + row_ptr[u]);
+                    }
                     place(u);
                 }
                 if (next < 0) break;
