@@ -636,9 +636,10 @@ int ensure_colours(lms_mesh_s* h) {
 }
 
 // Tile of the block Gauss-Seidel: the requested one, else about eight tiles per SM, at most 1,024
-// positions (on the 18.4M-vertex mesh larger tiles were slower: 0.66 / 0.75 / 0.80 ms per FP32 sweep
-// at 1,024 / 2,048 / 4,096).  From kBlockRangeTile up the sweep runs on the block-range layout (RDR,
-// FP32: 0.99 / 0.66 / 0.54 / 0.46 ms per sweep at 2^20 / 2^21 / 2^22 / 2^23 positions; coloured GS 0.39).
+// positions (on the 18.4M-vertex mesh in the BFS order larger tiles were slower: 0.66 / 0.75 / 0.80 ms
+// per FP32 sweep at 1,024 / 2,048 / 4,096; RDR 3.48 ms at 1,024).  From kBlockRangeTile up the sweep
+// runs on the block-range layout (RDR, FP32: 0.99 / 0.66 / 0.54 / 0.46 ms per sweep at 2^20 / 2^21 /
+// 2^22 / 2^23 positions; coloured GS 0.39).
 int32_t block_tile_for(const lms_mesh_s* h) {
     if (h->block_tile_req > 0) return h->block_tile_req;
     const int64_t want = int64_t(h->n) / (int64_t(h->sms) * 8);
